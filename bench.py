@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of one VMC step of the projected complex-RBM J1-J2 path on GB300.
+
+Workload (the 6x6 configuration): L = 6 periodic J1-J2 lattice, J2/J1 = 0.5,
+one complex RBM with M = 72 hidden units (alpha = 2) and biases, projected over
+the 36 translations x C4v (|G| = 288) and spin inversion (chi_P = +1), A1,
+K = (0,0); parameters N(0, 0.01^2) per real and imaginary part (seed 2206).
+
+One step = one pass of the hot path:
+  nnqs_sample         1024 chains x 16 kept samples, n_skip = 10, n_burn = 100
+                      (266,240 Metropolis proposals, each a full psi(s')/psi(s))
+  nnqs_local_energy   E_loc of the 16,384 samples (every anti-aligned J1/J2 bond
+                      -> one connected amplitude) with the FP64 sums of E_loc.
+Metric: projected-RBM amplitude evaluations per second (one evaluation = one
+psi(s') over all K|G| x 2 x M hidden terms: sampler proposals + connected
+configurations of E_loc + one fresh amplitude per sample), and E_loc
+samples/s; the same step in the plain FP64 GPU form is timed beside it.
+
+Timing: CUDA events on the launching stream, per step, with a 512 MB L2 flush
+before every timed step (outside the events); W warm-up steps; barrier and the
+maximum over ranks.  `e2e` repeats the step through the public API with the
+parameters copied host -> device every step and the E_loc sums copied back.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+L, J1, J2, ALPHA = 6, 1.0, 0.5, 2
+N = L * L
+M = ALPHA * N
+N_CHAINS, N_PER_CHAIN, N_SKIP, N_BURN = 1024, 16, 10, 100
+N_SAMPLES = N_CHAINS * N_PER_CHAIN
+PARAM_STD, PARAM_SEED = 0.01, 2206
+WORKLOAD = "6x6 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=72), 288 ops + spin inversion; 1024 chains x 16 samples"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
+FLOPS_PER_ELEMENT = 28   # one connected factor p e^D + (1-p) e^-D and its running product
+# DRAM bytes per k_ratio launch of this workload from the ncu capture summarised
+# in profiles/k_ratio_6x6.txt (None until captured for the current kernel)
+K_RATIO_TRAFFIC = None
+
+
+def bonds(L):
+    dx, dy = (1, 0, 1, 1), (0, 1, 1, -1)
+    out = []
+    for i in range(L * L):
+        x, y = i % L, i // L
+        for d in range(4):
+            out.append((i, ((x + dx[d]) % L) + L * ((y + dy[d]) % L)))
+    return np.array(out)
+
+
+def n_antialigned(words):
+    from paper_2206_14307_gb300 import synth
+    s = synth.unpack(words, N)
+    b = bonds(L)
+    return int((s[:, b[:, 0]] != s[:, b[:, 1]]).sum())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.p = None
+        return self
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(2)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) > 8 for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_2206_14307_gb300 import nnqs, synth
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    p = synth.random_params(N, M, 1, std=PARAM_STD, seed=PARAM_SEED)
+    pbuf = np.ascontiguousarray(np.stack([p.real, p.imag], -1))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec):
+        m = nnqs.Model(L, J1, J2, K=1, M=M, proj_t=True, proj_p=True, spin_inv=1, use_bias=True, precision=prec)
+        m.set_params(p)
+        return m
+
+    cfg = torch.empty(N_SAMPLES, 1, dtype=torch.int64, device="cuda")
+    acc = torch.empty(N_CHAINS, dtype=torch.float32, device="cuda")
+    eloc = torch.empty(N_SAMPLES, 2, dtype=torch.float64, device="cuda")
+    sums = torch.empty(4, dtype=torch.float64, device="cuda")
+    sums_host = torch.empty(4, dtype=torch.float64, pin_memory=True)
+    params_pinned = torch.from_numpy(pbuf.reshape(-1)).pin_memory()
+    params_dev = torch.empty_like(params_pinned, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def step(model, k, e2e=False):
+        seed = 14307 + 1000003 * rank + k
+        if e2e:
+            params_dev.copy_(params_pinned, non_blocking=True)
+            model.set_params(params_dev.view(-1, 2))
+        model.sample(seed, N_CHAINS, N_PER_CHAIN, N_SKIP, N_BURN, cfg_out=cfg, acc_out=acc)
+        model.local_energy(cfg, out=eloc, sums=sums)
+        if e2e:
+            sums_host.copy_(sums, non_blocking=True)
+
+    def timed(model, steps, warmup, e2e=False, ratio_events=False):
+        for k in range(warmup):
+            step(model, k, e2e)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        tot, tk = 0.0, 0.0
+        for k in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            seed = 14307 + 1000003 * rank + warmup + k
+            if e2e:
+                params_dev.copy_(params_pinned, non_blocking=True)
+                model.set_params(params_dev.view(-1, 2))
+            model.sample(seed, N_CHAINS, N_PER_CHAIN, N_SKIP, N_BURN, cfg_out=cfg, acc_out=acc)
+            ka.record(st)
+            model.local_energy(cfg, out=eloc, sums=sums)
+            kb.record(st)
+            if e2e:
+                sums_host.copy_(sums, non_blocking=True)
+            b.record(st)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+            tk += ka.elapsed_time(kb)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return tot / steps, tk / steps
+
+    m32 = make(nnqs.FP32)
+    with ClockSampler(dev) as clk:
+        ms, ms_eloc = timed(m32, args.steps, args.warmup)
+    m32.status()
+    e2e_ms, _ = timed(m32, args.steps, max(1, args.warmup // 2), e2e=True)
+    words = cfg.cpu().numpy().view(np.uint64)
+    nb = n_antialigned(words)
+    proposals = N_CHAINS * (N_BURN + N_PER_CHAIN * N_SKIP)
+    evals = proposals + nb + N_SAMPLES
+    G, nsign = m32.G, 2
+    elements = nb * G * nsign * M
+    res = dict(ms=ms, ms_eloc=ms_eloc, e2e_ms=e2e_ms, evals=evals, nb=nb, elements=elements,
+               clocks=clk.summary(), acc=float(acc.mean().item()), e_mean=float(eloc[:, 0].mean().item()) / N)
+    if not args.no_fp64:
+        m64 = make(nnqs.FP64)
+        ms64, ms64_eloc = timed(m64, args.fp64_steps, 1)
+        res.update(ms64=ms64, ms64_eloc=ms64_eloc)
+        m64.close()
+    m32.close()
+    return res
+
+
+def cpu_baseline(budget_s=20.0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+    import oracle
+    from paper_2206_14307_gb300 import synth
+    p = synth.random_params(N, M, 1, std=PARAM_STD, seed=PARAM_SEED)
+    om = oracle.Model(L, J1, J2, K=1, M=M, proj_t=True, proj_p=True, spin_inv=1, params=p)
+    cores = os.cpu_count() or 1
+    # sampler proposals: chains run in parallel (one per core)
+    t0 = time.perf_counter()
+    n_ch, steps = cores, 6
+    om.sample(14307, n_ch, 1, steps, 0)
+    t_prop = (time.perf_counter() - t0) / (n_ch * steps)        # wall seconds per proposal (all cores busy)
+    s = synth.random_sz0(N, 2 * cores, seed=307)
+    t0 = time.perf_counter()
+    om.local_energy(s)
+    t_eloc = (time.perf_counter() - t0) / len(s)
+    b = bonds(L)
+    nb_per = float((s[:, b[:, 0]] != s[:, b[:, 1]]).sum(1).mean())
+    proposals = N_CHAINS * (N_BURN + N_PER_CHAIN * N_SKIP)
+    step_s = proposals * t_prop + N_SAMPLES * t_eloc
+    evals = proposals + N_SAMPLES * (nb_per + 1)
+    return dict(value=evals / step_s, unit="amplitude evals/s", cores=cores, kind="oracle",
+                eloc_samples_per_s=1.0 / t_eloc,
+                sample=f"{n_ch * steps} sampler proposals ({n_ch} chains) + E_loc of {len(s)} random Sz=0 "
+                       f"configurations, extrapolated to one step of the workload")
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    oracle.build()
+    rates, erates = [], []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline()
+        if k >= args.warmup:
+            rates.append(cb["value"])
+            erates.append(cb["eloc_samples_per_s"])
+    v = float(np.mean(rates))
+    line = {"metric": "projected-RBM amplitude evals/s (E_loc samples/s beside)", "value": v,
+            "unit": "amplitude evals/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "eloc_samples_per_s": float(np.mean(erates)),
+            "cpu_baseline": {"value": v, "unit": "amplitude evals/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "amplitude evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="128 chains instead of 1024 (for profiler captures; not a bench line)")
+    args = ap.parse_args()
+    if args.small:
+        global N_CHAINS, N_SAMPLES
+        N_CHAINS = 128
+        N_SAMPLES = N_CHAINS * N_PER_CHAIN
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    from paper_2206_14307_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    res = gpu_arm(args, rank, world)
+    ms, e2e_ms = res["ms"], res["e2e_ms"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms, e2e_ms, res.get("ms64", 0.0)], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms, ms64 = t.tolist()
+        res["ms64"] = ms64
+    if rank != 0:
+        return
+    value = world * res["evals"] / (ms / 1e3)
+    eloc_ach = res["elements"] * FLOPS_PER_ELEMENT / (res["ms_eloc"] / 1e3) / 1e12
+    line = {
+        "metric": "projected-RBM amplitude evals/s (E_loc samples/s beside); FP32 form vs plain FP64 GPU form",
+        "value": value, "unit": "amplitude evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "M": M, "G": 288, "spin_inversion": True,
+                   "chains": N_CHAINS, "samples_per_chain": N_PER_CHAIN, "n_skip": N_SKIP, "n_burn": N_BURN,
+                   "precision": "FP32 (exact exponent tracking)", "l2": "flushed (512 MB write) before every step"},
+        "eloc_samples_per_s": world * N_SAMPLES / (ms / 1e3),
+        "acceptance": res["acc"], "E_loc_mean_per_site": res["e_mean"],
+        "roofline": {"kernel": "k_ratio (E_loc connected-amplitude engine)", "bound": "alu",
+                     "achieved": eloc_ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": eloc_ach / FP32_PEAK_TFLOPS, "traffic": K_RATIO_TRAFFIC,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",
+                     "work": f"{res['elements']} connected elements x {FLOPS_PER_ELEMENT} flop"},
+        "e2e": {"value": world * res["evals"] / (e2e_ms / 1e3), "unit": "amplitude evals/s",
+                "h2d_bytes_per_step": 2665 * 16, "d2h_bytes_per_step": 32},
+        "gpu_launches": 4 * args.steps,
+        "clocks": res["clocks"],
+    }
+    if "ms64" in res:
+        line["fp64_gpu"] = {"value": world * res["evals"] / (res["ms64"] / 1e3), "unit": "amplitude evals/s",
+                            "ms_per_step": res["ms64"], "steps": args.fp64_steps, "warmup": 1}
+        line["speedup_vs_fp64_gpu"] = res["ms64"] / ms
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"].pop("eloc_samples_per_s", None)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

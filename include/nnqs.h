@@ -1,0 +1,194 @@
+/*
+ * nnqs.h -- C ABI of the GB300 (sm_103a) library for batched variational Monte
+ * Carlo of the spin-1/2 J1-J2 Heisenberg model with symmetry-projected sums of
+ * complex restricted Boltzmann machines (Chen, Hendry, Weinberg, Feiguin,
+ * "Systematic improvement of neural network quantum states using a Lanczos
+ * recursion").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Lattice: L x L periodic square lattice, L even, 4 <= L <= 16; site
+ *    i = x + L*y; N = L*L (Sec. 3.4).
+ *  - Spins: s_i = 2 S^z_i = +-1.  The paper's RBM uses sigma = +-1/2
+ *    (Sec. 3.1, Eq. 2); with s = 2 sigma the weights and visible biases here
+ *    are half the paper's.
+ *  - Configuration encoding ("cfg"): ceil(N/64) little-endian uint64 words per
+ *    configuration, bit i set <=> s_i = +1.  Configurations passed to the
+ *    energy and Lanczos calls must lie in the Sz = 0 sector (N/2 bits set).
+ *  - Bonds (Eq. 1): for each site in increasing index, J1 (+x), J1 (+y),
+ *    J2 (+x+y), J2 (+x-y); 4N bonds.  H = sum_b J_b S_i.S_j with diagonal
+ *    J_b s_i s_j / 4 and off-diagonal J_b / 2 between configurations related
+ *    by exchanging an anti-aligned pair.
+ *  - Parameters: complex, K blocks of [log c_r, a_r[N], b_r[M], W_r[M][N]
+ *    row-major]; P = K (1 + N + M + M N).  The wave function is
+ *      psi(s) = sum_r c_r sum_{g in G} chi(g) [phi_r(T_g s) + chi_P phi_r(-T_g s)]
+ *    with phi_r(t) = exp(a_r . t) prod_m 2 cosh(b_rm + W_rm . t) (Eq. 2; the
+ *    bias-free Eq. 3 when use_bias = 0), G the translations (Eqs. 4-5) and/or
+ *    the C4v operations about site 0 (Eq. 6), chi(g) = exp(-i K.R) chi_I(L),
+ *    and the chi_P term present only with spin inversion.  The sum over r
+ *    (K > 1) forms the linear combination of RBMs of Sec. 3.1.
+ *  - Memory: every array argument is a DEVICE pointer owned by the caller
+ *    (unless stated otherwise), and every call is asynchronous on the given
+ *    CUDA stream (a cudaStream_t passed as void*; NULL = legacy default
+ *    stream).  The library owns only the opaque model: parameters, lookup
+ *    tables and a grow-only workspace.
+ *  - Errors: every call returns NNQS_OK (0) or a negative code; the message
+ *    of the last failure on the calling thread is nnqs_last_error().  No C++
+ *    exception crosses this boundary.  Device-side range faults (a non-finite
+ *    amplitude) are recorded in the model and reported by nnqs_status().
+ */
+#ifndef NNQS_H
+#define NNQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    NNQS_OK = 0,
+    NNQS_EINVAL = -1,       /* invalid argument or model description */
+    NNQS_ENOMEM = -2,       /* device allocation refused */
+    NNQS_ECUDA = -3,        /* CUDA runtime error (message in nnqs_last_error) */
+    NNQS_ETIMEOUT = -4,     /* a bounded device-side wait ran out */
+    NNQS_EUNSUPPORTED = -5, /* valid but unsupported size or combination */
+    NNQS_ERANGE = -6        /* a non-finite amplitude was produced on the device */
+};
+
+enum {
+    NNQS_FP64 = 0,   /* every step in double precision (the plain FP64 GPU form) */
+    NNQS_FP32 = 1,   /* FP32 arithmetic with exact binary exponent tracking */
+    NNQS_BF16X2 = 2, /* FP32, theta GEMM of fresh amplitudes on tcgen05 tensor
+                        cores with W split into two bf16 terms (hi + lo) */
+    NNQS_BF16X3 = 3  /* as BF16X2 with a three-term split (hi + mid + lo) */
+};
+
+enum { NNQS_A1 = 0, NNQS_A2 = 1, NNQS_B1 = 2, NNQS_B2 = 3 };
+enum { NNQS_K00 = 0, NNQS_KPIPI = 1, NNQS_KPI0 = 2, NNQS_K0PI = 3 };
+
+/* Model description (plain old data). */
+typedef struct nnqs_desc {
+    int32_t L;                    /* even, 4..16 */
+    double J1, J2;                /* Eq. 1 couplings */
+    int32_t K;                    /* number of RBMs in the linear combination, 1..8 */
+    int32_t M;                    /* hidden units per RBM, 1..512 */
+    int32_t project_translations; /* Eqs. 4-5: sum over all N translations */
+    int32_t project_point_group;  /* Eq. 6: sum over C4v (or its little group) */
+    int32_t momentum;             /* NNQS_K00 .. NNQS_K0PI; (pi,0),(0,pi) use the
+                                     little group {E, C2, sigma_x, sigma_y} */
+    int32_t irrep;                /* NNQS_A1 .. NNQS_B2 (B1: even under axis mirrors,
+                                     odd under diagonal mirrors) */
+    int32_t spin_inversion;       /* 0 = off, +1 / -1 = character chi_P */
+    int32_t use_bias;             /* 1: Eq. 2 with a, b; 0: bias-free Eq. 3 */
+    int32_t precision;            /* NNQS_FP64 .. NNQS_BF16X3 */
+} nnqs_desc;
+
+typedef struct nnqs_model nnqs_model;
+
+/* Creates a model on the current CUDA device: validates the description,
+ * builds the bond, permutation and character tables (Eqs. 1, 4-6) and
+ * allocates parameter storage (zero parameters).  Errors: NNQS_EINVAL for an
+ * invalid field or for spin_inversion = -1 without biases (the projection
+ * would vanish identically, Eq. 3); NNQS_EUNSUPPORTED for sizes beyond the
+ * limits above; NNQS_ENOMEM. */
+int nnqs_create(const nnqs_desc *desc, nnqs_model **out);
+
+/* Releases the model and its device memory (synchronises the device). */
+int nnqs_destroy(nnqs_model *model);
+
+/* Number of complex parameters P = K (1 + N + M + M N); -1 for NULL. */
+int64_t nnqs_num_params(const nnqs_model *model);
+
+/* Size of the symmetry group |G| used by the projection (Eqs. 4-6). */
+int32_t nnqs_group_size(const nnqs_model *model);
+
+/* Uploads parameters.  params: HOST pointer to P complex numbers stored as
+ * (re, im) double pairs in the layout above.  Derived device tables
+ * (transposed W, exp(+-2W), exp(+-2a), the bf16 split of W) are rebuilt on
+ * the stream.  The host buffer may be reused when the call returns. */
+int nnqs_set_params(nnqs_model *model, const double *params, int64_t P, void *stream);
+
+/* Same, from a DEVICE buffer of P (re, im) double pairs (e.g. after an
+ * SR update on the GPU). */
+int nnqs_set_params_device(nnqs_model *model, const double *params, int64_t P, void *stream);
+
+/* Metropolis-Hastings sampling of |psi|^2 with exchanges of anti-aligned
+ * spin pairs (Sec. 3.2).  One persistent chain per (n_chains); each chain
+ * keeps its per-hidden-unit amplitude cache on the device and updates it
+ * incrementally on every accepted exchange.
+ *   Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ *   (seed_lo, seed_hi ^ chain).  Initial state: Fisher-Yates shuffle of
+ *   N/2 up and N/2 down spins, driven by counters (q, 1, 0, 0).  Step t
+ *   (t = 0, 1, ... counting burn-in) uses counter (t, 0, 0, 0): words x0, x1
+ *   select the (x0 * N/2 >> 32)-th up site and the (x1 * N/2 >> 32)-th down
+ *   site in increasing site order; u = (x2 >> 8) * 2^-24 and the exchange is
+ *   accepted iff u < |psi(s')/psi(s)|^2.
+ *   After n_burn steps, a configuration is written after every n_skip steps.
+ * cfg_out: [n_chains * n_per_chain][ceil(N/64)] uint64, chain-major.
+ * acc_out: [n_chains] float, accepted fraction of the post-burn-in steps
+ *          (may be NULL).
+ * Errors: NNQS_EINVAL (non-positive counts), NNQS_ENOMEM (chain caches). */
+int nnqs_sample(nnqs_model *model, uint64_t seed, int32_t n_chains, int32_t n_per_chain,
+                int32_t n_skip, int32_t n_burn, uint64_t *cfg_out, float *acc_out, void *stream);
+
+/* log psi(s) for n configurations (Eqs. 2-6): logpsi_out [n][2] doubles
+ * (re, im), Im in (-pi, pi].  cfg: [n][ceil(N/64)].  With NNQS_BF16X2/X3 the
+ * theta products of all n*K*|G| transformed configurations run as one
+ * tcgen05 GEMM.  A configuration whose amplitude vanishes by symmetry
+ * returns re = -inf. */
+int nnqs_log_psi(nnqs_model *model, const uint64_t *cfg, int64_t n, double *logpsi_out, void *stream);
+
+/* Local energy (Sec. 3.2, Eq. 10): E_loc(s) = sum_s' H_{s s'} psi(s')/psi(s)
+ * over the anti-aligned J1 and J2 bonds.  eloc_out: [n][2] (re, im).
+ * sums_out (may be NULL): [4] doubles {sum Re E_loc, sum Im E_loc,
+ * sum |E_loc|^2, n}, accumulated in FP64 on the device. */
+int nnqs_local_energy(nnqs_model *model, const uint64_t *cfg, int64_t n, double *eloc_out,
+                      double *sums_out, void *stream);
+
+/* One Lanczos step (Sec. 3.3, Eqs. 13-18).  Per configuration
+ *   h1 = (H psi)(s)/psi(s)   and   h2 = (H^2 psi)(s)/psi(s)
+ * (h1_out, h2_out: [n][2], either may be NULL), and over all n samples of
+ * |psi|^2 the FP64 moments
+ *   moments_out[0..7] = {m0 = 1, m1 = <Re h1>, m2 = <|h1|^2>,
+ *                        m3 = <Re(conj(h1) h2)>, n, <Im h1>,
+ *                        <Im(conj(h1) h2)>, 0}
+ * and the p = 1 energy lanczos_out[0..2] = {E_p1, v, alpha} of the 2x2
+ * problem in span{psi0, psi1}:  v^2 = m2 - m1^2,
+ * d = (m3 - 3 m1 m2 + 2 m1^3) / (2 v^3), alpha = d - sqrt(d^2 + 1),
+ * E_p1 = m1 + v alpha (E_p1 = m1, alpha = 0 when v^2 <= 1e-14 m1^2).
+ * moments_out and lanczos_out are device buffers (either may be NULL). */
+int nnqs_lanczos_moments(nnqs_model *model, const uint64_t *cfg, int64_t n, double *h1_out,
+                         double *h2_out, double *moments_out, double *lanczos_out, void *stream);
+
+/* Log-derivatives O_k(s) = d log psi(s) / d alpha_k (holomorphic; Sec. 3.2,
+ * after Eq. 12), in parameter order.  O_out: [n][P][2] doubles. */
+int nnqs_grad_logpsi(nnqs_model *model, const uint64_t *cfg, int64_t n, double *O_out, void *stream);
+
+/* Energy gradient F_k = <conj(O_k) (E_loc - <E_loc>)> over n samples (the
+ * right-hand side of Eq. 12 without -dtau); for real coordinates
+ * dE/dRe alpha_k = 2 Re F_k and dE/dIm alpha_k = 2 Im F_k.
+ * O: [n][P][2], eloc: [n][2], F_out: [P][2] (all device, FP64). */
+int nnqs_energy_grad(const nnqs_model *model, const double *O, const double *eloc, int64_t n,
+                     double *F_out, void *stream);
+
+/* Matrix-free SR product (Eq. 12): y = (S + lambda I) x with
+ * S_kk' = <conj(O_k) O_k'> - <conj(O_k)><O_k'>, accumulated in FP64.
+ * O: [n][P][2], x, y: [P][2] (device). */
+int nnqs_sr_matvec(const nnqs_model *model, const double *O, int64_t n, const double *x,
+                   double lambda, double *y, void *stream);
+
+/* Device status word: NNQS_OK, or NNQS_ERANGE if a kernel produced a
+ * non-finite amplitude since the last call.  Synchronises the stream and
+ * clears the word. */
+int nnqs_status(nnqs_model *model, void *stream);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *nnqs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NNQS_H */

@@ -1,0 +1,466 @@
+// api.cu -- the C ABI of include/nnqs.h: argument validation, host-side
+// lattice and symmetry tables (Sec. 2.1 Eq. 1, Sec. 3.1 Eqs. 4-6), device
+// memory of the model, and dispatch to the kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nnqs.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace nnqs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(e == cudaErrorMemoryAllocation ? NNQS_ENOMEM : NNQS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define NNQS_CUDA(call)                                 \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Lattice tables
+// ---------------------------------------------------------------------------
+int site(int L, int x, int y) { return ((x % L + L) % L) + L * ((y % L + L) % L); }
+
+// J1 (+x), J1 (+y), J2 (+x+y), J2 (+x-y) for each site in increasing index
+void make_bonds(int L, std::vector<int16_t> &bi, std::vector<int16_t> &bj, std::vector<uint8_t> &bt)
+{
+    const int dx[4] = {1, 0, 1, 1}, dy[4] = {0, 1, 1, -1};
+    for (int i = 0; i < L * L; ++i)
+        for (int d = 0; d < 4; ++d) {
+            bi.push_back((int16_t)i);
+            bj.push_back((int16_t)site(L, i % L + dx[d], i / L + dy[d]));
+            bt.push_back(d < 2 ? 1 : 2);
+        }
+}
+
+// C4v element l acting on (x, y) about site 0: E, C4, C2, C4^3, x-mirror,
+// y-mirror, diagonal mirror, anti-diagonal mirror, as 2x2 integer matrices.
+const int kPoint[8][4] = {{1, 0, 0, 1},  {0, -1, 1, 0}, {-1, 0, 0, -1}, {0, 1, -1, 0},
+                          {-1, 0, 0, 1}, {1, 0, 0, -1}, {0, 1, 1, 0},   {0, -1, -1, 0}};
+// one-dimensional irreps (A1, A2, B1, B2) on the classes {E}, {C4, C4^3}, {C2},
+// {axis mirrors}, {diagonal mirrors}
+int c4v_character(int irrep, int l)
+{
+    const int rot = (l == 1 || l == 3) ? 1 : 0, axis = (l == 4 || l == 5), diag = (l == 6 || l == 7);
+    const int c4_sign = (irrep >= 2) ? -1 : 1;                 // B irreps are odd under C4
+    const int axis_sign = (irrep == 1 || irrep == 3) ? -1 : 1;  // A2, B2 odd under axis mirrors
+    int c = 1;
+    if (rot) c = c4_sign;
+    if (axis) c = axis_sign;
+    if (diag) c = c4_sign * axis_sign;  // sigma_d = C4 * sigma_axis
+    return c;
+}
+
+int make_group(const nnqs_desc &d, std::vector<uint8_t> &perm, std::vector<double> &chi)
+{
+    const int L = d.L, N = L * L;
+    std::vector<int> ops;
+    if (!d.project_point_group) ops = {0};
+    else if (d.momentum == NNQS_K00 || d.momentum == NNQS_KPIPI) ops = {0, 1, 2, 3, 4, 5, 6, 7};
+    else ops = {0, 2, 4, 5};  // little group of (pi,0) / (0,pi)
+    const int nt = d.project_translations ? N : 1;
+    int G = 0;
+    for (int l : ops)
+        for (int t = 0; t < nt; ++t) {
+            const int m = t % L, n = t / L;
+            int ph = 1;
+            if (d.momentum == NNQS_KPIPI && ((m + n) & 1)) ph = -1;
+            if (d.momentum == NNQS_KPI0 && (m & 1)) ph = -1;
+            if (d.momentum == NNQS_K0PI && (n & 1)) ph = -1;
+            chi.push_back((double)(ph * c4v_character(d.irrep, l)));
+            const int *R = kPoint[l];
+            for (int i = 0; i < N; ++i) {
+                const int x = i % L, y = i / L;
+                perm.push_back((uint8_t)site(L, R[0] * x + R[1] * y + m, R[2] * x + R[3] * y + n));
+            }
+            ++G;
+        }
+    return G;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Model
+// ---------------------------------------------------------------------------
+struct nnqs_model {
+    nnqs_desc d;
+    int N, G, nsign, nwords, nbonds, nsm, device;
+    int64_t P;
+    bool fp64;
+    uint8_t *perm = nullptr;
+    int16_t *bi = nullptr, *bj = nullptr;
+    uint8_t *bt = nullptr;
+    void *chi = nullptr;
+    double *params = nullptr;
+    void *Wt = nullptr, *b = nullptr, *a = nullptr, *logc = nullptr, *X = nullptr, *XA = nullptr;
+    int *status = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace {
+
+template <typename T> DevModel<T> view(const nnqs_model *m)
+{
+    DevModel<T> v;
+    v.L = m->d.L; v.N = m->N; v.K = m->d.K; v.M = m->d.M; v.G = m->G; v.nsign = m->nsign;
+    v.use_bias = m->d.use_bias; v.nbonds = m->nbonds; v.nwords = m->nwords; v.chiP = m->d.spin_inversion;
+    v.J1 = (T)m->d.J1; v.J2 = (T)m->d.J2;
+    v.perm = m->perm; v.chi = (const T *)m->chi;
+    v.Wt = (const cx<T> *)m->Wt; v.bvec = (const cx<T> *)m->b; v.avec = (const cx<T> *)m->a;
+    v.logc = (const cx<T> *)m->logc; v.X = (const cx2<T> *)m->X; v.XA = (const cx2<T> *)m->XA;
+    v.bond_i = m->bi; v.bond_j = m->bj; v.bond_t = m->bt;
+    v.status = m->status;
+    return v;
+}
+
+int ensure_ws(nnqs_model *m, size_t bytes)
+{
+    if (bytes <= m->ws_bytes) return NNQS_OK;
+    if (m->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(m->ws);
+        m->ws = nullptr;
+        m->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&m->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NNQS_ENOMEM, "workspace of %zu bytes refused: %s", bytes, cudaGetErrorString(e));
+    }
+    m->ws_bytes = bytes;
+    return NNQS_OK;
+}
+
+int check_model(const nnqs_model *m)
+{
+    if (!m) return fail(NNQS_EINVAL, "model is NULL");
+    return NNQS_OK;
+}
+
+template <typename F> int with_device(const nnqs_model *m, F &&f)
+{
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != m->device) cudaSetDevice(m->device);
+    const int rc = f();
+    if (cur != m->device && cur >= 0) cudaSetDevice(cur);
+    return rc;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+const char *nnqs_last_error(void) { return g_err.c_str(); }
+
+int nnqs_create(const nnqs_desc *desc, nnqs_model **out)
+{
+    if (!desc || !out) return fail(NNQS_EINVAL, "desc and out must be non-NULL");
+    *out = nullptr;
+    const nnqs_desc d = *desc;
+    if (d.L < 4 || (d.L & 1)) return fail(NNQS_EUNSUPPORTED, "L must be even and >= 4 (got %d)", d.L);
+    if (d.L > kMaxL) return fail(NNQS_EUNSUPPORTED, "L > %d is not supported", kMaxL);
+    if (d.K < 1 || d.K > kMaxK) return fail(NNQS_EUNSUPPORTED, "K must be in 1..%d", kMaxK);
+    if (d.M < 1 || d.M > kMaxM) return fail(NNQS_EUNSUPPORTED, "M must be in 1..%d", kMaxM);
+    if (d.momentum < 0 || d.momentum > 3) return fail(NNQS_EINVAL, "momentum must be 0..3");
+    if (d.irrep < 0 || d.irrep > 3) return fail(NNQS_EINVAL, "irrep must be 0..3");
+    if (d.spin_inversion < -1 || d.spin_inversion > 1) return fail(NNQS_EINVAL, "spin_inversion must be -1, 0 or 1");
+    if (!d.use_bias && d.spin_inversion == -1)
+        return fail(NNQS_EINVAL, "spin_inversion = -1 without biases: the projection vanishes identically");
+    if (d.precision < NNQS_FP64 || d.precision > NNQS_BF16X3) return fail(NNQS_EINVAL, "unknown precision %d", d.precision);
+    if (!(d.J1 == d.J1) || !(d.J2 == d.J2)) return fail(NNQS_EINVAL, "J1, J2 must be finite");
+
+    nnqs_model *m = new nnqs_model();
+    m->d = d;
+    m->N = d.L * d.L;
+    m->nwords = (m->N + 63) / 64;
+    m->nsign = d.spin_inversion ? 2 : 1;
+    m->P = (int64_t)d.K * (1 + m->N + d.M + (int64_t)d.M * m->N);
+    m->fp64 = d.precision == NNQS_FP64;
+    cudaGetDevice(&m->device);
+    cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, m->device);
+
+    std::vector<int16_t> bi, bj;
+    std::vector<uint8_t> bt, perm;
+    std::vector<double> chi;
+    make_bonds(d.L, bi, bj, bt);
+    m->nbonds = (int)bi.size();
+    m->G = make_group(d, perm, chi);
+
+    auto cleanup = [&](int rc) { nnqs_destroy(m); return rc; };
+    const size_t ts = m->fp64 ? sizeof(double) : sizeof(float);
+    const size_t K = d.K, M = d.M, N = m->N;
+#define ALLOC(ptr, bytes)                                                        \
+    do {                                                                         \
+        cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes));                   \
+        if (e_ != cudaSuccess) { cudaGetLastError(); return cleanup(cuda_fail(e_, "cudaMalloc")); } \
+    } while (0)
+    ALLOC(m->perm, perm.size());
+    ALLOC(m->bi, bi.size() * 2);
+    ALLOC(m->bj, bj.size() * 2);
+    ALLOC(m->bt, bt.size());
+    ALLOC(m->chi, chi.size() * ts);
+    ALLOC(m->params, (size_t)m->P * 2 * sizeof(double));
+    ALLOC(m->Wt, K * N * M * 2 * ts);
+    ALLOC(m->b, K * M * 2 * ts);
+    ALLOC(m->a, K * N * 2 * ts);
+    ALLOC(m->logc, K * 2 * ts);
+    ALLOC(m->X, K * N * M * 4 * ts);
+    ALLOC(m->XA, K * N * 4 * ts);
+    ALLOC(m->status, sizeof(int));
+#undef ALLOC
+    cudaMemcpy(m->perm, perm.data(), perm.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(m->bi, bi.data(), bi.size() * 2, cudaMemcpyHostToDevice);
+    cudaMemcpy(m->bj, bj.data(), bj.size() * 2, cudaMemcpyHostToDevice);
+    cudaMemcpy(m->bt, bt.data(), bt.size(), cudaMemcpyHostToDevice);
+    if (m->fp64) {
+        cudaMemcpy(m->chi, chi.data(), chi.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> cf(chi.begin(), chi.end());
+        cudaMemcpy(m->chi, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice);
+    }
+    cudaMemset(m->status, 0, sizeof(int));
+    std::vector<double> zero((size_t)m->P * 2, 0.0);
+    cudaError_t e = cudaMemcpy(m->params, zero.data(), zero.size() * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMemcpy"));
+    *out = m;
+    return nnqs_set_params_device(m, m->params, m->P, nullptr) == NNQS_OK ? (cudaDeviceSynchronize(), NNQS_OK)
+                                                                           : cleanup(NNQS_ECUDA);
+}
+
+int nnqs_destroy(nnqs_model *m)
+{
+    if (!m) return NNQS_OK;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {m->perm, m->bi, m->bj, m->bt, m->chi, m->params, m->Wt, m->b, m->a, m->logc, m->X, m->XA, m->status, m->ws};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete m;
+    return NNQS_OK;
+}
+
+int64_t nnqs_num_params(const nnqs_model *m) { return m ? m->P : -1; }
+int32_t nnqs_group_size(const nnqs_model *m) { return m ? m->G : -1; }
+
+int nnqs_set_params_device(nnqs_model *m, const double *params, int64_t P, void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (!params) return fail(NNQS_EINVAL, "params is NULL");
+    if (P != m->P) return fail(NNQS_EINVAL, "expected %lld parameters, got %lld", (long long)m->P, (long long)P);
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        if (params != m->params)
+            NNQS_CUDA(cudaMemcpyAsync(m->params, params, (size_t)P * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        cudaError_t e;
+        if (m->fp64)
+            e = launch_build_tables<double>(m->params, m->N, m->d.M, m->d.K, (cx<double> *)m->Wt, (cx<double> *)m->b,
+                                            (cx<double> *)m->a, (cx<double> *)m->logc, (cx2<double> *)m->X,
+                                            (cx2<double> *)m->XA, st);
+        else
+            e = launch_build_tables<float>(m->params, m->N, m->d.M, m->d.K, (cx<float> *)m->Wt, (cx<float> *)m->b,
+                                           (cx<float> *)m->a, (cx<float> *)m->logc, (cx2<float> *)m->X,
+                                           (cx2<float> *)m->XA, st);
+        if (e != cudaSuccess) return cuda_fail(e, "build tables");
+        return NNQS_OK;
+    });
+}
+
+int nnqs_set_params(nnqs_model *m, const double *params, int64_t P, void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (!params) return fail(NNQS_EINVAL, "params is NULL");
+    if (P != m->P) return fail(NNQS_EINVAL, "expected %lld parameters, got %lld", (long long)m->P, (long long)P);
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        NNQS_CUDA(cudaMemcpyAsync(m->params, params, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+        NNQS_CUDA(cudaStreamSynchronize(st));  // the host buffer may be reused on return
+        return nnqs_set_params_device(m, m->params, P, stream);
+    });
+}
+
+int nnqs_log_psi(nnqs_model *m, const uint64_t *cfg, int64_t n, double *out, void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n < 0) return fail(NNQS_EINVAL, "n < 0");
+    if (n == 0) return NNQS_OK;
+    if (!cfg || !out) return fail(NNQS_EINVAL, "cfg and logpsi_out must be non-NULL");
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = m->fp64 ? launch_log_psi(view<double>(m), cfg, n, out, m->nsm, st)
+                                : launch_log_psi(view<float>(m), cfg, n, out, m->nsm, st);
+        return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "log_psi");
+    });
+}
+
+int nnqs_local_energy(nnqs_model *m, const uint64_t *cfg, int64_t n, double *eloc, double *sums, void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n < 0) return fail(NNQS_EINVAL, "n < 0");
+    if (n == 0) return NNQS_OK;
+    if (!cfg || !eloc) return fail(NNQS_EINVAL, "cfg and eloc_out must be non-NULL");
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 0, eloc, nullptr, m->nsm, st)
+                                : launch_ratio(view<float>(m), cfg, n, 0, eloc, nullptr, m->nsm, st);
+        if (e != cudaSuccess) return cuda_fail(e, "local_energy");
+        if (sums) {
+            const int nb = 64;
+            int rc = ensure_ws(m, nb * 6 * sizeof(double));
+            if (rc) return rc;
+            e = launch_eloc_sums(eloc, n, (double *)m->ws, nb, sums, st);
+            if (e != cudaSuccess) return cuda_fail(e, "eloc sums");
+        }
+        return NNQS_OK;
+    });
+}
+
+int nnqs_lanczos_moments(nnqs_model *m, const uint64_t *cfg, int64_t n, double *h1, double *h2, double *moments,
+                         double *lanczos, void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n < 0) return fail(NNQS_EINVAL, "n < 0");
+    if (n == 0) return NNQS_OK;
+    if (!cfg) return fail(NNQS_EINVAL, "cfg must be non-NULL");
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        const int nb = 64;
+        size_t need = align256(nb * 6 * sizeof(double));
+        const size_t off_h1 = need;
+        if (!h1) need += align256((size_t)n * 2 * sizeof(double));
+        const size_t off_h2 = need;
+        if (!h2) need += align256((size_t)n * 2 * sizeof(double));
+        int rc = ensure_ws(m, need);
+        if (rc) return rc;
+        char *ws = (char *)m->ws;
+        double *H1 = h1 ? h1 : (double *)(ws + off_h1);
+        double *H2 = h2 ? h2 : (double *)(ws + off_h2);
+        cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, H1, H2, m->nsm, st)
+                                : launch_ratio(view<float>(m), cfg, n, 1, H1, H2, m->nsm, st);
+        if (e != cudaSuccess) return cuda_fail(e, "lanczos");
+        if (moments || lanczos) {
+            e = launch_moments(H1, H2, n, (double *)ws, nb, moments, lanczos, st);
+            if (e != cudaSuccess) return cuda_fail(e, "moments");
+        }
+        return NNQS_OK;
+    });
+}
+
+int nnqs_sample(nnqs_model *m, uint64_t seed, int32_t n_chains, int32_t n_per_chain, int32_t n_skip, int32_t n_burn,
+                uint64_t *cfg_out, float *acc_out, void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n_chains <= 0 || n_per_chain <= 0 || n_skip <= 0 || n_burn < 0)
+        return fail(NNQS_EINVAL, "n_chains, n_per_chain, n_skip must be > 0 and n_burn >= 0");
+    if (!cfg_out) return fail(NNQS_EINVAL, "cfg_out must be non-NULL");
+    if ((int64_t)n_burn + (int64_t)n_per_chain * n_skip > 0x7fffffffLL)
+        return fail(NNQS_EINVAL, "total number of steps exceeds 2^31 - 1");
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t per = m->fp64 ? sampler_cache_bytes(view<double>(m)) : sampler_cache_bytes(view<float>(m));
+        int rc = ensure_ws(m, per * (size_t)n_chains);
+        if (rc) return rc;
+        cudaError_t e = m->fp64
+                            ? launch_sample(view<double>(m), seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, m->ws, st)
+                            : launch_sample(view<float>(m), seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, m->ws, st);
+        return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "sample");
+    });
+}
+
+int nnqs_grad_logpsi(nnqs_model *m, const uint64_t *cfg, int64_t n, double *O, void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n < 0) return fail(NNQS_EINVAL, "n < 0");
+    if (n == 0) return NNQS_OK;
+    if (!cfg || !O) return fail(NNQS_EINVAL, "cfg and O_out must be non-NULL");
+    if ((size_t)m->G * m->N > 200 * 1024) return fail(NNQS_EUNSUPPORTED, "|G| * N too large for the gradient kernel");
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e;
+        if (m->fp64) {
+            const DevModel<double> v = view<double>(m);
+            const int grid = grad_grid(v, n, m->nsm);
+            int rc = ensure_ws(m, grad_scratch_bytes(v) * grid);
+            if (rc) return rc;
+            e = launch_grad(v, cfg, n, O, m->ws, grid, st);
+        } else {
+            const DevModel<float> v = view<float>(m);
+            const int grid = grad_grid(v, n, m->nsm);
+            int rc = ensure_ws(m, grad_scratch_bytes(v) * grid);
+            if (rc) return rc;
+            e = launch_grad(v, cfg, n, O, m->ws, grid, st);
+        }
+        return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "grad_logpsi");
+    });
+}
+
+int nnqs_energy_grad(const nnqs_model *mc, const double *O, const double *eloc, int64_t n, double *F, void *stream)
+{
+    nnqs_model *m = const_cast<nnqs_model *>(mc);
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n <= 0) return fail(NNQS_EINVAL, "n must be > 0");
+    if (!O || !eloc || !F) return fail(NNQS_EINVAL, "O, eloc and F_out must be non-NULL");
+    return with_device(m, [&]() -> int {
+        int rc = ensure_ws(m, 256);
+        if (rc) return rc;
+        cudaError_t e = launch_energy_grad(O, eloc, n, m->P, F, (double *)m->ws, (cudaStream_t)stream);
+        return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "energy_grad");
+    });
+}
+
+int nnqs_sr_matvec(const nnqs_model *mc, const double *O, int64_t n, const double *x, double lambda, double *y, void *stream)
+{
+    nnqs_model *m = const_cast<nnqs_model *>(mc);
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n <= 0) return fail(NNQS_EINVAL, "n must be > 0");
+    if (!O || !x || !y) return fail(NNQS_EINVAL, "O, x and y must be non-NULL");
+    return with_device(m, [&]() -> int {
+        int rc = ensure_ws(m, align256((size_t)(2 * n + 2) * sizeof(double)));
+        if (rc) return rc;
+        cudaError_t e = launch_sr_matvec(O, n, m->P, x, lambda, y, (double *)m->ws, (cudaStream_t)stream);
+        return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "sr_matvec");
+    });
+}
+
+int nnqs_status(nnqs_model *m, void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        int h = 0;
+        NNQS_CUDA(cudaStreamSynchronize(st));
+        NNQS_CUDA(cudaMemcpy(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost));
+        NNQS_CUDA(cudaMemset(m->status, 0, sizeof(int)));
+        if (h) return fail(h, "a kernel produced a non-finite amplitude");
+        return NNQS_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,208 @@
+// common.cuh -- device-side types and arithmetic shared by the kernels of the
+// projected-RBM VMC library (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nnqs {
+
+constexpr int kMaxL = 16;
+constexpr int kMaxN = kMaxL * kMaxL;
+constexpr int kMaxWords = (kMaxN + 63) / 64;
+constexpr int kMaxM = 512;
+constexpr int kMaxK = 8;
+constexpr int kWarps = 8;           // warps per CTA of the amplitude kernels
+constexpr int kThreads = kWarps * 32;
+
+// ---------------------------------------------------------------------------
+// Complex numbers
+// ---------------------------------------------------------------------------
+template <typename T> struct alignas(2 * sizeof(T)) cx { T x, y; };
+template <typename T> struct alignas(4 * sizeof(T) > 16 ? 16 : 4 * sizeof(T)) cx2 { cx<T> a, b; };
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T x, T y) { return cx<T>{x, y}; }
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
+{
+    return cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return cx<T>{a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return cx<T>{a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return cx<T>{a.x * s, a.y * s}; }
+template <typename T> __device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b)
+{
+    T d = T(1) / (b.x * b.x + b.y * b.y);
+    return cx<T>{(a.x * b.x + a.y * b.y) * d, (a.y * b.x - a.x * b.y) * d};
+}
+
+// ---------------------------------------------------------------------------
+// Scaled complex numbers: value = (x + i y) * 2^e with an exact integer
+// binary exponent, so that products of hundreds of hidden-unit factors and
+// sums over thousands of symmetry terms never leave the FP32 range and lose
+// no absolute accuracy in log psi.
+// ---------------------------------------------------------------------------
+template <typename T> struct sc { T x, y; int e; };
+
+template <typename T> __device__ __forceinline__ T pow2i(int k);
+template <> __device__ __forceinline__ float pow2i<float>(int k)
+{
+    if (k < -126) return 0.f;
+    if (k > 127) k = 127;
+    return __int_as_float((127 + k) << 23);
+}
+template <> __device__ __forceinline__ double pow2i<double>(int k)
+{
+    if (k < -1022) return 0.0;
+    if (k > 1023) k = 1023;
+    return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
+// binary exponent of max(|x|,|y|) (0 for zero / non-finite inputs)
+template <typename T> __device__ __forceinline__ int expo(T x, T y);
+template <> __device__ __forceinline__ int expo<float>(float x, float y)
+{
+    float m = fmaxf(fabsf(x), fabsf(y));
+    int b = (__float_as_int(m) >> 23) & 0xff;
+    return (b == 0 || b == 0xff) ? 0 : b - 127;
+}
+template <> __device__ __forceinline__ int expo<double>(double x, double y)
+{
+    double m = fmax(fabs(x), fabs(y));
+    int b = (int)((__double_as_longlong(m) >> 52) & 0x7ff);
+    return (b == 0 || b == 0x7ff) ? 0 : b - 1023;
+}
+
+template <typename T> __device__ __forceinline__ sc<T> sc_norm(sc<T> v)
+{
+    int k = expo<T>(v.x, v.y);
+    T s = pow2i<T>(-k);
+    return sc<T>{v.x * s, v.y * s, v.e + k};
+}
+template <typename T> __device__ __forceinline__ sc<T> sc_mul(sc<T> a, sc<T> b)
+{
+    cx<T> p = cmul(mk(a.x, a.y), mk(b.x, b.y));
+    return sc_norm(sc<T>{p.x, p.y, a.e + b.e});
+}
+template <typename T> __device__ __forceinline__ bool sc_zero(sc<T> a) { return a.x == T(0) && a.y == T(0); }
+template <typename T> __device__ __forceinline__ bool sc_finite(sc<T> v) { return isfinite(v.x) && isfinite(v.y); }
+__device__ __forceinline__ void flag_range(int *status) { atomicExch(status, -6); }
+
+template <typename T> __device__ __forceinline__ sc<T> sc_add(sc<T> a, sc<T> b)
+{
+    if (sc_zero(b)) return a;
+    if (sc_zero(a)) return b;
+    if (b.e > a.e) { sc<T> t = a; a = b; b = t; }
+    T s = pow2i<T>(b.e - a.e);
+    return sc_norm(sc<T>{a.x + b.x * s, a.y + b.y * s, a.e});
+}
+
+template <typename T> __device__ __forceinline__ T shfl_x(T v, int lane_mask)
+{
+    return __shfl_xor_sync(0xffffffffu, v, lane_mask);
+}
+// product over the 32 lanes of a warp (every lane receives it)
+template <typename T> __device__ __forceinline__ sc<T> warp_prod(sc<T> v)
+{
+    v = sc_norm(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sc<T> w{shfl_x(v.x, o), shfl_x(v.y, o), __shfl_xor_sync(0xffffffffu, v.e, o)};
+        v = sc_mul(v, w);
+    }
+    return v;
+}
+template <typename T> __device__ __forceinline__ sc<T> warp_sum_sc(sc<T> v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sc<T> w{shfl_x(v.x, o), shfl_x(v.y, o), __shfl_xor_sync(0xffffffffu, v.e, o)};
+        v = sc_add(v, w);
+    }
+    return v;
+}
+template <typename T> __device__ __forceinline__ cx<T> warp_sum(cx<T> v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) { v.x += shfl_x(v.x, o); v.y += shfl_x(v.y, o); }
+    return v;
+}
+
+// exp(z) as a scaled number (exact exponent split of Re z)
+template <typename T> __device__ __forceinline__ sc<T> sc_exp(cx<T> z)
+{
+    const T l2e = T(1.4426950408889634);
+    T t = z.x * l2e;
+    T k = floor(t);
+    T m = exp2(t - k);
+    T s, c;
+    sincos(z.y, &s, &c);
+    return sc<T>{m * c, m * s, (int)k};
+}
+
+// 2 cosh(theta) = mant * 2^k  together with  p = e^theta / (2 cosh theta).
+// With u = |Re theta| and v = sign(Re theta) Im theta (cosh is even):
+//   2 cosh = e^u [e^{iv} + e^{-2u} e^{-iv}] = 2^k e^f [cos v (1+q) + i sin v (1-q)]
+// where u log2(e) = k + f, q = e^{-2u} <= 1; and e^{theta'}/(2cosh) =
+// e^f e^{iv} / mant for theta' = sign(Re theta) theta, p(theta) = 1 - p(-theta).
+template <typename T>
+__device__ __forceinline__ void cosh2(cx<T> th, cx<T> &mant, int &k, cx<T> &p)
+{
+    const T l2e = T(1.4426950408889634);
+    bool neg = th.x < T(0);
+    T u = fabs(th.x);
+    T v = neg ? -th.y : th.y;
+    T t = u * l2e;
+    T kf = floor(t);
+    T ef = exp2(t - kf);
+    T q = exp2(T(-2) * t);
+    T sv, cv;
+    sincos(v, &sv, &cv);
+    mant = cx<T>{ef * cv * (T(1) + q), ef * sv * (T(1) - q)};
+    k = (int)kf;
+    cx<T> pp = cdiv(cx<T>{ef * cv, ef * sv}, mant);
+    p = neg ? cx<T>{T(1) - pp.x, -pp.y} : pp;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+struct u32x4 { uint32_t v[4]; };
+__device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return u32x4{{c0, c1, c2, c3}};
+}
+
+// ---------------------------------------------------------------------------
+// Device view of a model (passed by value to kernels)
+// ---------------------------------------------------------------------------
+template <typename T> struct DevModel {
+    int L, N, K, M, G, nsign, use_bias, nbonds, nwords, chiP;
+    T J1, J2;
+    const uint8_t *perm;    // [G][N]   image of site i under g
+    const T *chi;           // [G]      +-1
+    const cx<T> *Wt;        // [K][N][M] transposed weights
+    const cx<T> *bvec;      // [K][M]
+    const cx<T> *avec;      // [K][N]
+    const cx<T> *logc;      // [K]
+    const cx2<T> *X;        // [K][N][M]  (exp(-2W_mk), exp(+2W_mk))
+    const cx2<T> *XA;       // [K][N]     (exp(-2a_k),  exp(+2a_k))
+    const int16_t *bond_i;  // [4N]
+    const int16_t *bond_j;  // [4N]
+    const uint8_t *bond_t;  // [4N] 1 = J1, 2 = J2
+    int *status;            // device status word
+};
+
+template <typename T> __device__ __forceinline__ T bondJ(const DevModel<T> &md, int b)
+{
+    return md.bond_t[b] == 1 ? md.J1 : md.J2;
+}
+
+__device__ __forceinline__ int spin_of(const uint64_t *w, int i) { return ((w[i >> 6] >> (i & 63)) & 1ull) ? 1 : -1; }
+
+}  // namespace nnqs

@@ -1,0 +1,243 @@
+// k_reduce.cu -- FP64 reductions (moments of Sec. 3.3, E_loc sums, the energy
+// gradient and the SR product of Eq. 12) and the parameter-derived tables.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nnqs {
+
+constexpr int kRedThreads = 256;
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) sh[0][q] += sh[w][q];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = sh[0][q];
+    }
+}
+
+// stage 1: per-block sums over a contiguous range of samples
+__global__ void __launch_bounds__(kRedThreads) k_moments_partial(const double *__restrict__ h1,
+                                                                 const double *__restrict__ h2, int64_t n,
+                                                                 double *__restrict__ partial)
+{
+    __shared__ double sh[kRedThreads / 32][6];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = per * blockIdx.x, hi = lo + per < n ? lo + per : n;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const double ax = h1[2 * k], ay = h1[2 * k + 1];
+        v[0] += 1.0;
+        v[1] += ax;
+        v[2] += ax * ax + ay * ay;
+        v[4] += ay;
+        if (h2) {
+            const double bx = h2[2 * k], by = h2[2 * k + 1];
+            v[3] += ax * bx + ay * by;   // Re(conj(h1) h2)
+            v[5] += ax * by - ay * bx;   // Im(conj(h1) h2)
+        }
+    }
+    block_sum<6>(v, sh);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 6; ++q) partial[blockIdx.x * 6 + q] = v[q];
+}
+
+// stage 2: fixed-order sum of the partials, moments and the p = 1 Lanczos step
+__global__ void __launch_bounds__(32) k_moments_final(const double *__restrict__ partial, int nb,
+                                                      double *__restrict__ moments, double *__restrict__ lanczos)
+{
+    if (threadIdx.x != 0) return;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int q = 0; q < 6; ++q) v[q] += partial[b * 6 + q];
+    const double z = v[0] > 0 ? v[0] : 1.0;
+    const double m1 = v[1] / z, m2 = v[2] / z, m3 = v[3] / z;
+    if (moments) {
+        moments[0] = 1.0; moments[1] = m1; moments[2] = m2; moments[3] = m3;
+        moments[4] = v[0]; moments[5] = v[4] / z; moments[6] = v[5] / z; moments[7] = 0.0;
+    }
+    if (lanczos) {
+        // lowest eigenpair of the 2x2 matrix of H in span{psi0, psi1}
+        const double v2 = m2 - m1 * m1;
+        if (v2 <= 1e-14 * m1 * m1 || v2 <= 0.0) {
+            lanczos[0] = m1; lanczos[1] = v2 > 0.0 ? sqrt(v2) : 0.0; lanczos[2] = 0.0;
+        } else {
+            const double vv = sqrt(v2);
+            const double d = (m3 - 3.0 * m1 * m2 + 2.0 * m1 * m1 * m1) / (2.0 * v2 * vv);
+            const double al = d - sqrt(d * d + 1.0);
+            lanczos[0] = m1 + vv * al; lanczos[1] = vv; lanczos[2] = al;
+        }
+    }
+}
+
+cudaError_t launch_moments(const double *h1, const double *h2, int64_t n, double *partial, int nblocks,
+                           double *moments, double *lanczos, cudaStream_t st)
+{
+    k_moments_partial<<<nblocks, kRedThreads, 0, st>>>(h1, h2, n, partial);
+    k_moments_final<<<1, 32, 0, st>>>(partial, nblocks, moments, lanczos);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(32) k_eloc_final(const double *__restrict__ partial, int nb, double *__restrict__ sums)
+{
+    if (threadIdx.x != 0) return;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int q = 0; q < 6; ++q) v[q] += partial[b * 6 + q];
+    sums[0] = v[1]; sums[1] = v[4]; sums[2] = v[2]; sums[3] = v[0];
+}
+
+cudaError_t launch_eloc_sums(const double *eloc, int64_t n, double *partial, int nblocks, double *sums, cudaStream_t st)
+{
+    k_moments_partial<<<nblocks, kRedThreads, 0, st>>>(eloc, nullptr, n, partial);
+    k_eloc_final<<<1, 32, 0, st>>>(partial, nblocks, sums);
+    return cudaGetLastError();
+}
+
+// mean of a complex vector (one block, fixed order)
+__global__ void __launch_bounds__(kRedThreads) k_cmean(const double *__restrict__ v, int64_t n, double *__restrict__ out)
+{
+    __shared__ double sh[kRedThreads / 32][2];
+    double a[2] = {0, 0};
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) { a[0] += v[2 * k]; a[1] += v[2 * k + 1]; }
+    block_sum<2>(a, sh);
+    if (threadIdx.x == 0) { out[0] = a[0] / (double)n; out[1] = a[1] / (double)n; }
+}
+
+// F_k = (1/n) sum_s conj(O_sk) (e_s - ebar)
+__global__ void k_energy_grad(const double *__restrict__ O, const double *__restrict__ e, const double *__restrict__ ebar,
+                              int64_t n, int64_t P, double *__restrict__ F)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const double bx = ebar[0], by = ebar[1];
+    double fx = 0, fy = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
+        const double dx = e[2 * s] - bx, dy = e[2 * s + 1] - by;
+        fx += ox * dx + oy * dy;
+        fy += ox * dy - oy * dx;
+    }
+    F[2 * k] = fx / (double)n;
+    F[2 * k + 1] = fy / (double)n;
+}
+
+cudaError_t launch_energy_grad(const double *O, const double *eloc, int64_t n, int64_t P, double *F, double *scratch,
+                               cudaStream_t st)
+{
+    k_cmean<<<1, kRedThreads, 0, st>>>(eloc, n, scratch);
+    const int tb = 256;
+    k_energy_grad<<<(unsigned)((P + tb - 1) / tb), tb, 0, st>>>(O, eloc, scratch, n, P, F);
+    return cudaGetLastError();
+}
+
+// z_s = sum_k O_sk x_k  (one block per sample)
+__global__ void __launch_bounds__(kRedThreads) k_ov(const double *__restrict__ O, const double *__restrict__ x, int64_t P,
+                                                    double *__restrict__ z)
+{
+    __shared__ double sh[kRedThreads / 32][2];
+    const int64_t s = blockIdx.x;
+    double a[2] = {0, 0};
+    for (int64_t k = threadIdx.x; k < P; k += blockDim.x) {
+        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
+        const double xx = x[2 * k], xy = x[2 * k + 1];
+        a[0] += ox * xx - oy * xy;
+        a[1] += ox * xy + oy * xx;
+    }
+    block_sum<2>(a, sh);
+    if (threadIdx.x == 0) { z[2 * s] = a[0]; z[2 * s + 1] = a[1]; }
+}
+
+// y_k = (1/n) sum_s conj(O_sk) z_s - conj(Obar_k) zbar + lambda x_k
+__global__ void k_sr_out(const double *__restrict__ O, const double *__restrict__ z, const double *__restrict__ zbar,
+                         const double *__restrict__ x, double lambda, int64_t n, int64_t P, double *__restrict__ y)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    double ax = 0, ay = 0, mx = 0, my = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
+        const double zx = z[2 * s], zy = z[2 * s + 1];
+        ax += ox * zx + oy * zy;
+        ay += ox * zy - oy * zx;
+        mx += ox; my += oy;
+    }
+    const double inv = 1.0 / (double)n;
+    ax *= inv; ay *= inv; mx *= inv; my *= inv;
+    const double bx = zbar[0], by = zbar[1];
+    y[2 * k] = ax - (mx * bx + my * by) + lambda * x[2 * k];
+    y[2 * k + 1] = ay - (mx * by - my * bx) + lambda * x[2 * k + 1];
+}
+
+cudaError_t launch_sr_matvec(const double *O, int64_t n, int64_t P, const double *x, double lambda, double *y,
+                             double *scratch, cudaStream_t st)
+{
+    double *z = scratch;            // [n][2]
+    double *zbar = scratch + 2 * n; // [2]
+    k_ov<<<(unsigned)n, kRedThreads, 0, st>>>(O, x, P, z);
+    k_cmean<<<1, kRedThreads, 0, st>>>(z, n, zbar);
+    const int tb = 256;
+    k_sr_out<<<(unsigned)((P + tb - 1) / tb), tb, 0, st>>>(O, z, zbar, x, lambda, n, P, y);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// parameter-derived tables (computed in FP64, stored in T)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_tables(const double *__restrict__ par, int N, int M, int K, cx<T> *Wt, cx<T> *b, cx<T> *a, cx<T> *logc,
+                         cx2<T> *X, cx2<T> *XA)
+{
+    const int64_t P1 = 1 + N + M + (int64_t)M * N;
+    const int64_t tot = (int64_t)K * P1;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(q / P1);
+        const int64_t o = q - r * P1;
+        const double vx = par[2 * q], vy = par[2 * q + 1];
+        if (o == 0) {
+            logc[r] = cx<T>{(T)vx, (T)vy};
+        } else if (o < 1 + N) {
+            const int k = (int)(o - 1);
+            a[(size_t)r * N + k] = cx<T>{(T)vx, (T)vy};
+            double s, c;
+            sincos(2.0 * vy, &s, &c);
+            const double em = exp(-2.0 * vx), ep = exp(2.0 * vx);
+            XA[(size_t)r * N + k] = cx2<T>{cx<T>{(T)(em * c), (T)(-em * s)}, cx<T>{(T)(ep * c), (T)(ep * s)}};
+        } else if (o < 1 + N + M) {
+            b[(size_t)r * M + (o - 1 - N)] = cx<T>{(T)vx, (T)vy};
+        } else {
+            const int64_t wq = o - 1 - N - M;
+            const int m = (int)(wq / N), k = (int)(wq - (int64_t)m * N);
+            const size_t t = ((size_t)r * N + k) * M + m;
+            Wt[t] = cx<T>{(T)vx, (T)vy};
+            double s, c;
+            sincos(2.0 * vy, &s, &c);
+            const double em = exp(-2.0 * vx), ep = exp(2.0 * vx);
+            X[t] = cx2<T>{cx<T>{(T)(em * c), (T)(-em * s)}, cx<T>{(T)(ep * c), (T)(ep * s)}};
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_build_tables(const double *params, int N, int M, int K, cx<T> *Wt, cx<T> *b, cx<T> *a, cx<T> *logc,
+                                cx2<T> *X, cx2<T> *XA, cudaStream_t st)
+{
+    k_tables<T><<<1024, 256, 0, st>>>(params, N, M, K, Wt, b, a, logc, X, XA);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_build_tables<float>(const double *, int, int, int, cx<float> *, cx<float> *, cx<float> *, cx<float> *, cx2<float> *, cx2<float> *, cudaStream_t);
+template cudaError_t launch_build_tables<double>(const double *, int, int, int, cx<double> *, cx<double> *, cx<double> *, cx<double> *, cx2<double> *, cx2<double> *, cudaStream_t);
+
+}  // namespace nnqs

@@ -1,0 +1,54 @@
+// kernels.h -- launchers of the device kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace nnqs {
+
+int mpl_slot(int M);
+
+// `nsm`: streaming multiprocessors of the device; grids are sized from it and
+// the kernels' occupancy.
+template <typename T>
+cudaError_t launch_log_psi(const DevModel<T> &md, const uint64_t *cfg, int64_t n, double *out, int nsm,
+                           cudaStream_t st);
+
+// mode 0: h1 only (E_loc); mode 1: h1 and h2 (Lanczos)
+template <typename T>
+cudaError_t launch_ratio(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int mode, double *h1, double *h2,
+                         int nsm, cudaStream_t st);
+
+// Bytes of per-chain cache the sampler needs.
+template <typename T> size_t sampler_cache_bytes(const DevModel<T> &md);
+
+template <typename T>
+cudaError_t launch_sample(const DevModel<T> &md, uint64_t seed, int n_chains, int n_per_chain, int n_skip, int n_burn,
+                          uint64_t *cfg_out, float *acc_out, void *cache, cudaStream_t st);
+
+// Per-CTA scratch of the gradient kernel (U, V rows) and its grid size.
+template <typename T> size_t grad_scratch_bytes(const DevModel<T> &md);
+template <typename T> int grad_grid(const DevModel<T> &md, int64_t n, int nsm);
+
+template <typename T>
+cudaError_t launch_grad(const DevModel<T> &md, const uint64_t *cfg, int64_t n, double *O, void *scratch, int grid,
+                        cudaStream_t st);
+
+// FP64 reductions
+cudaError_t launch_moments(const double *h1, const double *h2, int64_t n, double *partial, int nblocks,
+                           double *moments, double *lanczos, cudaStream_t st);
+cudaError_t launch_eloc_sums(const double *eloc, int64_t n, double *partial, int nblocks, double *sums,
+                             cudaStream_t st);
+cudaError_t launch_energy_grad(const double *O, const double *eloc, int64_t n, int64_t P, double *F, double *scratch,
+                               cudaStream_t st);
+cudaError_t launch_sr_matvec(const double *O, int64_t n, int64_t P, const double *x, double lambda, double *y,
+                             double *scratch, cudaStream_t st);
+
+// parameter-derived tables
+template <typename T>
+cudaError_t launch_build_tables(const double *params, int N, int M, int K, cx<T> *Wt, cx<T> *b, cx<T> *a, cx<T> *logc,
+                                cx2<T> *X, cx2<T> *XA, cudaStream_t st);
+
+}  // namespace nnqs

@@ -1,0 +1,234 @@
+"""Thin Python binding of the C ABI in include/nnqs.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library ``libnnqs_gb300.so``;
+PyTorch only provides device memory and streams.  Importing this module on a
+machine without the built library raises immediately -- there is no fallback.
+
+Functions with the ABI's names (``nnqs_create``, ``nnqs_log_psi``, ...) take
+raw pointers as Python ints; the ``Model`` class wraps them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnnqs_gb300.so")
+
+NNQS_OK, NNQS_EINVAL, NNQS_ENOMEM, NNQS_ECUDA, NNQS_ETIMEOUT, NNQS_EUNSUPPORTED, NNQS_ERANGE = 0, -1, -2, -3, -4, -5, -6
+FP64, FP32, BF16X2, BF16X3 = 0, 1, 2, 3
+A1, A2, B1, B2 = 0, 1, 2, 3
+K00, KPIPI, KPI0, K0PI = 0, 1, 2, 3
+
+# exported symbols of include/nnqs.h
+ABI_FUNCTIONS = (
+    "nnqs_create", "nnqs_destroy", "nnqs_num_params", "nnqs_group_size", "nnqs_set_params",
+    "nnqs_set_params_device", "nnqs_sample", "nnqs_log_psi", "nnqs_local_energy",
+    "nnqs_lanczos_moments", "nnqs_grad_logpsi", "nnqs_energy_grad", "nnqs_sr_matvec",
+    "nnqs_status", "nnqs_last_error",
+)
+
+
+class nnqs_desc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("J1", ctypes.c_double), ("J2", ctypes.c_double),
+                ("K", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("project_translations", ctypes.c_int32), ("project_point_group", ctypes.c_int32),
+                ("momentum", ctypes.c_int32), ("irrep", ctypes.c_int32),
+                ("spin_inversion", ctypes.c_int32), ("use_bias", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+class NNQSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nnqs error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2206_14307_gb300.build.build() "
+                              "(no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, u64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "nnqs_create": ([ctypes.POINTER(nnqs_desc), ctypes.POINTER(P)], ctypes.c_int),
+            "nnqs_destroy": ([P], ctypes.c_int),
+            "nnqs_num_params": ([P], i64),
+            "nnqs_group_size": ([P], i32),
+            "nnqs_set_params": ([P, P, i64, P], ctypes.c_int),
+            "nnqs_set_params_device": ([P, P, i64, P], ctypes.c_int),
+            "nnqs_sample": ([P, u64, i32, i32, i32, i32, P, P, P], ctypes.c_int),
+            "nnqs_log_psi": ([P, P, i64, P, P], ctypes.c_int),
+            "nnqs_local_energy": ([P, P, i64, P, P, P], ctypes.c_int),
+            "nnqs_lanczos_moments": ([P, P, i64, P, P, P, P, P], ctypes.c_int),
+            "nnqs_grad_logpsi": ([P, P, i64, P, P], ctypes.c_int),
+            "nnqs_energy_grad": ([P, P, P, i64, P, P], ctypes.c_int),
+            "nnqs_sr_matvec": ([P, P, i64, P, d, P, P], ctypes.c_int),
+            "nnqs_status": ([P, P], ctypes.c_int),
+            "nnqs_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != NNQS_OK:
+        raise NNQSError(rc, lib().nnqs_last_error().decode())
+    return rc
+
+
+# ---- raw ABI (same names; pointers are Python ints) -------------------------------------------
+def nnqs_create(desc: nnqs_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().nnqs_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def nnqs_destroy(h): return _check(lib().nnqs_destroy(h))
+def nnqs_num_params(h): return lib().nnqs_num_params(h)
+def nnqs_group_size(h): return lib().nnqs_group_size(h)
+def nnqs_set_params(h, params_host_ptr, P, stream=0): return _check(lib().nnqs_set_params(h, params_host_ptr, P, stream))
+def nnqs_set_params_device(h, params_ptr, P, stream=0): return _check(lib().nnqs_set_params_device(h, params_ptr, P, stream))
+
+
+def nnqs_sample(h, seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, stream=0):
+    return _check(lib().nnqs_sample(h, seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, stream))
+
+
+def nnqs_log_psi(h, cfg, n, out, stream=0): return _check(lib().nnqs_log_psi(h, cfg, n, out, stream))
+def nnqs_local_energy(h, cfg, n, eloc, sums, stream=0): return _check(lib().nnqs_local_energy(h, cfg, n, eloc, sums, stream))
+
+
+def nnqs_lanczos_moments(h, cfg, n, h1, h2, moments, lanczos, stream=0):
+    return _check(lib().nnqs_lanczos_moments(h, cfg, n, h1, h2, moments, lanczos, stream))
+
+
+def nnqs_grad_logpsi(h, cfg, n, O, stream=0): return _check(lib().nnqs_grad_logpsi(h, cfg, n, O, stream))
+def nnqs_energy_grad(h, O, eloc, n, F, stream=0): return _check(lib().nnqs_energy_grad(h, O, eloc, n, F, stream))
+def nnqs_sr_matvec(h, O, n, x, lam, y, stream=0): return _check(lib().nnqs_sr_matvec(h, O, n, x, lam, y, stream))
+def nnqs_status(h, stream=0): return _check(lib().nnqs_status(h, stream))
+
+
+# ---- torch convenience wrapper ---------------------------------------------------------------
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Model:
+    """A model on the current CUDA device.  Tensors are torch CUDA tensors:
+    configurations int64 [n][ceil(N/64)] (the bits of the uint64 words),
+    complex results float64 [n][2]."""
+
+    def __init__(self, L, J1=1.0, J2=0.5, K=1, M=None, proj_t=False, proj_p=False, momentum=K00, irrep=A1,
+                 spin_inv=0, use_bias=True, precision=FP32):
+        self.L, self.N = L, L * L
+        self.M = M if M is not None else self.N
+        self.K = K
+        self.desc = nnqs_desc(L, J1, J2, K, self.M, int(proj_t), int(proj_p), momentum, irrep,
+                              spin_inv, int(use_bias), precision)
+        self.h = nnqs_create(self.desc)
+        self.P = nnqs_num_params(self.h)
+        self.G = nnqs_group_size(self.h)
+        self.nwords = (self.N + 63) // 64
+
+    def close(self):
+        if getattr(self, "h", None):
+            nnqs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        """params: complex numpy array (host) or float64 CUDA tensor [P][2]."""
+        import torch
+        if isinstance(params, torch.Tensor):
+            assert params.is_cuda and params.dtype == torch.float64
+            nnqs_set_params_device(self.h, params.data_ptr(), self.P, _stream())
+        else:
+            p = np.asarray(params, np.complex128).reshape(-1)
+            buf = np.ascontiguousarray(np.stack([p.real, p.imag], -1))
+            nnqs_set_params(self.h, buf.ctypes.data, self.P, _stream())
+
+    def _out(self, *shape):
+        import torch
+        return torch.empty(*shape, dtype=torch.float64, device="cuda")
+
+    def log_psi(self, cfg, out=None):
+        n = cfg.shape[0]
+        out = self._out(n, 2) if out is None else out
+        nnqs_log_psi(self.h, cfg.data_ptr(), n, out.data_ptr(), _stream())
+        return out
+
+    def local_energy(self, cfg, out=None, sums=None):
+        n = cfg.shape[0]
+        out = self._out(n, 2) if out is None else out
+        nnqs_local_energy(self.h, cfg.data_ptr(), n, out.data_ptr(), _ptr(sums), _stream())
+        return out
+
+    def lanczos(self, cfg, h1=None, h2=None, moments=None, lanczos=None):
+        n = cfg.shape[0]
+        h1 = self._out(n, 2) if h1 is None else h1
+        h2 = self._out(n, 2) if h2 is None else h2
+        moments = self._out(8) if moments is None else moments
+        lanczos = self._out(3) if lanczos is None else lanczos
+        nnqs_lanczos_moments(self.h, cfg.data_ptr(), n, h1.data_ptr(), h2.data_ptr(), moments.data_ptr(),
+                             lanczos.data_ptr(), _stream())
+        return h1, h2, moments, lanczos
+
+    def sample(self, seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out=None, acc_out=None):
+        import torch
+        if cfg_out is None:
+            cfg_out = torch.empty(n_chains * n_per_chain, self.nwords, dtype=torch.int64, device="cuda")
+        if acc_out is None:
+            acc_out = torch.empty(n_chains, dtype=torch.float32, device="cuda")
+        nnqs_sample(self.h, seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out.data_ptr(), acc_out.data_ptr(),
+                    _stream())
+        return cfg_out, acc_out
+
+    def grad_logpsi(self, cfg, out=None):
+        n = cfg.shape[0]
+        out = self._out(n, self.P, 2) if out is None else out
+        nnqs_grad_logpsi(self.h, cfg.data_ptr(), n, out.data_ptr(), _stream())
+        return out
+
+    def energy_grad(self, O, eloc, out=None):
+        n = O.shape[0]
+        out = self._out(self.P, 2) if out is None else out
+        nnqs_energy_grad(self.h, O.data_ptr(), eloc.data_ptr(), n, out.data_ptr(), _stream())
+        return out
+
+    def sr_matvec(self, O, x, lam, out=None):
+        n = O.shape[0]
+        out = self._out(self.P, 2) if out is None else out
+        nnqs_sr_matvec(self.h, O.data_ptr(), n, x.data_ptr(), float(lam), out.data_ptr(), _stream())
+        return out
+
+    def status(self):
+        return nnqs_status(self.h, _stream())
+
+
+def cfg_tensor(words: np.ndarray):
+    """uint64 numpy words -> int64 CUDA tensor with the same bits."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(words).view(np.int64)).cuda()

@@ -1,0 +1,79 @@
+"""Shared test helpers: matching model descriptions for the oracle and the
+CUDA library, seeded inputs, and the comparison rules."""
+import numpy as np
+
+import oracle
+from paper_2206_14307_gb300 import synth
+
+# BASELINE-style workloads (shapes only; values are seeded synthetic)
+CONFIG_4x4 = dict(L=4, J2=0.5, K=1, alpha=1, proj=False, spin_inv=0)
+CONFIG_6x6 = dict(L=6, J2=0.5, K=1, alpha=2, proj=True, spin_inv=1)
+CONFIG_10x10 = dict(L=10, J2=0.5, K=4, alpha=4, proj=True, spin_inv=0)
+CONFIG_8x8 = dict(L=8, J2=0.5, K=1, alpha=2, proj=True, spin_inv=0)
+
+
+def make_pair(L, J2=0.5, K=1, alpha=1, M=None, proj=False, spin_inv=0, use_bias=True, momentum=0, irrep=0,
+              std=0.01, seed=2206, precision=1, logc_std=None):
+    from paper_2206_14307_gb300 import nnqs
+    N = L * L
+    M = M if M is not None else alpha * N
+    p = synth.random_params(N, M, K, std=std, seed=seed, logc_std=logc_std)
+    om = oracle.Model(L, 1.0, J2, K=K, M=M, proj_t=proj, proj_p=proj, momentum=momentum, irrep=irrep,
+                      spin_inv=spin_inv, use_bias=use_bias, params=p)
+    gm = nnqs.Model(L, 1.0, J2, K=K, M=M, proj_t=proj, proj_p=proj, momentum=momentum, irrep=irrep,
+                    spin_inv=spin_inv, use_bias=use_bias, precision=precision)
+    gm.set_params(p)
+    return om, gm, p
+
+
+def wrap_dphase(a, b):
+    d = (np.asarray(a) - np.asarray(b)) % (2 * np.pi)
+    return np.minimum(d, 2 * np.pi - d)
+
+
+def assert_logpsi_close(got, want, atol):
+    got = np.asarray(got)
+    want = np.asarray(want)
+    fin = np.isfinite(want.real)
+    assert np.array_equal(fin, np.isfinite(got.real))
+    assert np.max(np.abs(got.real[fin] - want.real[fin]), initial=0) <= atol
+    assert np.max(wrap_dphase(got.imag[fin], want.imag[fin]), initial=0) <= atol
+
+
+def to_complex(t):
+    a = t.detach().cpu().numpy()
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def annihilated(L, spins, proj, momentum=0, irrep=0, spin_inv=0, use_bias=True):
+    """Configurations whose projected amplitude vanishes identically: fixed by
+    a group element g (or by g combined with spin inversion) whose character
+    is -1, since then psi(s) = chi(g) psi(s) (Eqs. 4-6).  Without biases every
+    RBM is even under s -> -s (Eq. 3), which acts as inversion with chi_P = +1.
+    E_loc is 0/0 there."""
+    s = np.asarray(spins)
+    if not use_bias and not spin_inv:
+        spin_inv = 1
+    if not proj:
+        return np.zeros(len(s), bool)
+    perm, chi = oracle.group(L, True, True, momentum, irrep)
+    out = np.zeros(len(s), bool)
+    for k, x in enumerate(s):
+        for g in range(len(perm)):
+            t = np.empty_like(x)
+            t[perm[g]] = x
+            if chi[g] < 0 and np.array_equal(t, x):
+                out[k] = True
+                break
+            if spin_inv and chi[g] * spin_inv < 0 and np.array_equal(t, -x):
+                out[k] = True
+                break
+    return out
+
+
+def fp32_rtol(std):
+    """Per-sample relative tolerance of FP32 ratios: ~1e-7 per factor times the
+    conditioning 1/|cosh(theta)| of the nearest zero, which grows with the
+    weight scale; 1e-5 at the workloads' std <= 0.05, 1e-4 at the 0.3 stress
+    scale."""
+    return 1e-5 if std <= 0.05 else 1e-4
