@@ -48,7 +48,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
                 print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, srcs))
     if _stale(LIB, objs):
         tmp = LIB + ".tmp"

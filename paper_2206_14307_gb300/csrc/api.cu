@@ -118,6 +118,8 @@ struct nnqs_model {
     void *chi = nullptr;
     double *params = nullptr;
     void *Wt = nullptr, *b = nullptr, *a = nullptr, *logc = nullptr, *X = nullptr, *XA = nullptr;
+    void *Tb = nullptr, *Cb = nullptr, *S4 = nullptr, *CS = nullptr;
+    uint16_t *bperm = nullptr;
     int *status = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -135,6 +137,8 @@ template <typename T> DevModel<T> view(const nnqs_model *m)
     v.Wt = (const cx<T> *)m->Wt; v.bvec = (const cx<T> *)m->b; v.avec = (const cx<T> *)m->a;
     v.logc = (const cx<T> *)m->logc; v.X = (const cx2<T> *)m->X; v.XA = (const cx2<T> *)m->XA;
     v.bond_i = m->bi; v.bond_j = m->bj; v.bond_t = m->bt;
+    v.Tb = (const cx<T> *)m->Tb; v.Cb = (const cx<T> *)m->Cb; v.S4 = (const cx<T> *)m->S4; v.CS = (const cx<T> *)m->CS;
+    v.bperm = m->bperm;
     v.status = m->status;
     return v;
 }
@@ -235,9 +239,31 @@ int nnqs_create(const nnqs_desc *desc, nnqs_model **out)
     ALLOC(m->logc, K * 2 * ts);
     ALLOC(m->X, K * N * M * 4 * ts);
     ALLOC(m->XA, K * N * 4 * ts);
+    ALLOC(m->Tb, K * 2 * bi.size() * M * 2 * ts);
+    ALLOC(m->Cb, K * bi.size() * 2 * ts);
+    ALLOC(m->S4, K * 2 * N * M * 2 * ts);
+    ALLOC(m->CS, K * N * 2 * ts);
+    ALLOC(m->bperm, (size_t)m->G * bi.size() * sizeof(uint16_t));
     ALLOC(m->status, sizeof(int));
 #undef ALLOC
     cudaMemcpy(m->perm, perm.data(), perm.size(), cudaMemcpyHostToDevice);
+    {
+        // image of every bond under every group element, with the orientation flag
+        std::vector<int> index((size_t)N * N, -1);
+        for (size_t b = 0; b < bi.size(); ++b) {
+            index[(size_t)bi[b] * N + bj[b]] = (int)b;
+            index[(size_t)bj[b] * N + bi[b]] = (int)b;
+        }
+        std::vector<uint16_t> bp((size_t)m->G * bi.size());
+        for (int g = 0; g < m->G; ++g)
+            for (size_t b = 0; b < bi.size(); ++b) {
+                const int gi = perm[(size_t)g * N + bi[b]], gj = perm[(size_t)g * N + bj[b]];
+                const int img = index[(size_t)gi * N + gj];
+                if (img < 0) return cleanup(fail(NNQS_EINVAL, "symmetry operation does not map bonds to bonds"));
+                bp[(size_t)g * bi.size() + b] = (uint16_t)(img | (bi[img] != gi ? 0x8000 : 0));
+            }
+        cudaMemcpy(m->bperm, bp.data(), bp.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    }
     cudaMemcpy(m->bi, bi.data(), bi.size() * 2, cudaMemcpyHostToDevice);
     cudaMemcpy(m->bj, bj.data(), bj.size() * 2, cudaMemcpyHostToDevice);
     cudaMemcpy(m->bt, bt.data(), bt.size(), cudaMemcpyHostToDevice);
@@ -260,7 +286,8 @@ int nnqs_destroy(nnqs_model *m)
 {
     if (!m) return NNQS_OK;
     cudaDeviceSynchronize();
-    void *ptrs[] = {m->perm, m->bi, m->bj, m->bt, m->chi, m->params, m->Wt, m->b, m->a, m->logc, m->X, m->XA, m->status, m->ws};
+    void *ptrs[] = {m->perm, m->bi, m->bj, m->bt, m->chi, m->params, m->Wt, m->b, m->a, m->logc, m->X, m->XA,
+                    m->Tb, m->Cb, m->S4, m->CS, m->bperm, m->status, m->ws};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -289,6 +316,15 @@ int nnqs_set_params_device(nnqs_model *m, const double *params, int64_t P, void 
                                            (cx<float> *)m->a, (cx<float> *)m->logc, (cx2<float> *)m->X,
                                            (cx2<float> *)m->XA, st);
         if (e != cudaSuccess) return cuda_fail(e, "build tables");
+        if (m->fp64)
+            e = launch_tables_conn<double>(m->params, m->N, m->d.M, m->d.K, m->nbonds, m->d.use_bias, m->bi, m->bj,
+                                           (cx<double> *)m->Tb, (cx<double> *)m->Cb, (cx<double> *)m->S4,
+                                           (cx<double> *)m->CS, st);
+        else
+            e = launch_tables_conn<float>(m->params, m->N, m->d.M, m->d.K, m->nbonds, m->d.use_bias, m->bi, m->bj,
+                                          (cx<float> *)m->Tb, (cx<float> *)m->Cb, (cx<float> *)m->S4,
+                                          (cx<float> *)m->CS, st);
+        if (e != cudaSuccess) return cuda_fail(e, "build connection tables");
         return NNQS_OK;
     });
 }
@@ -385,11 +421,13 @@ int nnqs_sample(nnqs_model *m, uint64_t seed, int32_t n_chains, int32_t n_per_ch
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
         const size_t per = m->fp64 ? sampler_cache_bytes(view<double>(m)) : sampler_cache_bytes(view<float>(m));
+        const int conc = m->fp64 ? sampler_grid(view<double>(m), n_chains, m->nsm) : sampler_grid(view<float>(m), n_chains, m->nsm);
+        (void)conc;
         int rc = ensure_ws(m, per * (size_t)n_chains);
         if (rc) return rc;
         cudaError_t e = m->fp64
-                            ? launch_sample(view<double>(m), seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, m->ws, st)
-                            : launch_sample(view<float>(m), seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, m->ws, st);
+                            ? launch_sample(view<double>(m), seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, m->ws, m->nsm, st)
+                            : launch_sample(view<float>(m), seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, m->ws, m->nsm, st);
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "sample");
     });
 }

@@ -192,6 +192,14 @@ template <typename T> struct DevModel {
     const cx<T> *logc;      // [K]
     const cx2<T> *X;        // [K][N][M]  (exp(-2W_mk), exp(+2W_mk))
     const cx2<T> *XA;       // [K][N]     (exp(-2a_k),  exp(+2a_k))
+    // connected-configuration tables (bond b' = (a, b) of the bond list,
+    // D0_m = -2 (W_ma - W_mb) the change of theta_m when s_a = +1, s_b = -1
+    // are exchanged):
+    const cx<T> *Tb;        // [K][2][4N][M]  exp(+2 D0_m) - 1, exp(-2 D0_m) - 1
+    const cx<T> *Cb;        // [K][4N]        -2 (a_a - a_b) + 2 sum_m (W_ma - W_mb)
+    const cx<T> *S4;        // [K][2][N][M]   exp(-4 W_mk), exp(+4 W_mk)
+    const cx<T> *CS;        // [K][N]         sum_m W_mk
+    const uint16_t *bperm;  // [G][4N]        image bond of b under g | (orientation flip << 15)
     const int16_t *bond_i;  // [4N]
     const int16_t *bond_j;  // [4N]
     const uint8_t *bond_t;  // [4N] 1 = J1, 2 = J2

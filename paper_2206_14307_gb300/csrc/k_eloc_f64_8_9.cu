@@ -1,0 +1,7 @@
+// double instantiation of the connected-configuration engine, GL = 8, MPL = 9.
+#include "k_eloc.cuh"
+
+namespace nnqs {
+template cudaError_t launch_eloc_variant<double, 8, 9>(const DevModel<double> &, const uint64_t *, int64_t, int, int,
+                                                          double *, double *, int, cudaStream_t);
+}  // namespace nnqs

@@ -229,6 +229,91 @@ __global__ void k_tables(const double *__restrict__ par, int N, int M, int K, cx
     }
 }
 
+// e^{z} - 1 without cancellation for small z
+__device__ __forceinline__ void cexpm1(double x, double y, double &re, double &im)
+{
+    double sy, cy;
+    sincos(y, &sy, &cy);
+    const double sh = sin(0.5 * y);
+    re = expm1(x) * cy - 2.0 * sh * sh;
+    im = exp(x) * sy;
+}
+
+template <typename T>
+__global__ void k_tables_conn(const double *__restrict__ par, int N, int M, int K, int nb, int use_bias,
+                              const int16_t *__restrict__ bi, const int16_t *__restrict__ bj, cx<T> *Tb, cx<T> *Cb,
+                              cx<T> *S4, cx<T> *CS)
+{
+    const int64_t P1 = 1 + N + M + (int64_t)M * N;
+    const int64_t n1 = (int64_t)K * nb * M, n2 = (int64_t)K * N * M, n3 = (int64_t)K * nb, n4 = (int64_t)K * N;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n1 + n2 + n3 + n4;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (q < n1) {
+            const int r = (int)(q / ((int64_t)nb * M));
+            const int64_t rem = q - (int64_t)r * nb * M;
+            const int b = (int)(rem / M), m = (int)(rem - (int64_t)b * M);
+            const double *W = par + 2 * (r * P1 + 1 + N + M + (int64_t)m * N);
+            const int a = bi[b], c = bj[b];
+            const double zx = -4.0 * (W[2 * a] - W[2 * c]), zy = -4.0 * (W[2 * a + 1] - W[2 * c + 1]);
+            double px, py, mx, my;
+            cexpm1(zx, zy, px, py);
+            cexpm1(-zx, -zy, mx, my);
+            Tb[(((size_t)r * 2 + 0) * nb + b) * M + m] = cx<T>{(T)px, (T)py};
+            Tb[(((size_t)r * 2 + 1) * nb + b) * M + m] = cx<T>{(T)mx, (T)my};
+        } else if (q < n1 + n2) {
+            const int64_t u = q - n1;
+            const int r = (int)(u / ((int64_t)N * M));
+            const int64_t rem = u - (int64_t)r * N * M;
+            const int k = (int)(rem / M), m = (int)(rem - (int64_t)k * M);
+            const double *W = par + 2 * (r * P1 + 1 + N + M + (int64_t)m * N + k);
+            double s, c;
+            sincos(4.0 * W[1], &s, &c);
+            const double em = exp(-4.0 * W[0]), ep = exp(4.0 * W[0]);
+            S4[(((size_t)r * 2 + 0) * N + k) * M + m] = cx<T>{(T)(em * c), (T)(-em * s)};
+            S4[(((size_t)r * 2 + 1) * N + k) * M + m] = cx<T>{(T)(ep * c), (T)(ep * s)};
+        } else if (q < n1 + n2 + n3) {
+            const int64_t u = q - n1 - n2;
+            const int r = (int)(u / nb), b = (int)(u - (int64_t)r * nb);
+            const double *base = par + 2 * r * P1;
+            const int a = bi[b], c = bj[b];
+            double sx = 0, sy = 0;
+            for (int m = 0; m < M; ++m) {
+                const double *W = base + 2 * (1 + N + M + (int64_t)m * N);
+                sx += W[2 * a] - W[2 * c];
+                sy += W[2 * a + 1] - W[2 * c + 1];
+            }
+            double cx_ = 2.0 * sx, cy_ = 2.0 * sy;
+            if (use_bias) {
+                cx_ -= 2.0 * (base[2 * (1 + a)] - base[2 * (1 + c)]);
+                cy_ -= 2.0 * (base[2 * (1 + a) + 1] - base[2 * (1 + c) + 1]);
+            }
+            Cb[(size_t)r * nb + b] = cx<T>{(T)cx_, (T)cy_};
+        } else {
+            const int64_t u = q - n1 - n2 - n3;
+            const int r = (int)(u / N), k = (int)(u - (int64_t)r * N);
+            const double *base = par + 2 * r * P1;
+            double sx = 0, sy = 0;
+            for (int m = 0; m < M; ++m) {
+                const double *W = base + 2 * (1 + N + M + (int64_t)m * N + k);
+                sx += W[0];
+                sy += W[1];
+            }
+            CS[(size_t)r * N + k] = cx<T>{(T)sx, (T)sy};
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_tables_conn(const double *params, int N, int M, int K, int nb, int use_bias, const int16_t *bi,
+                               const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, cudaStream_t st)
+{
+    k_tables_conn<T><<<2048, 256, 0, st>>>(params, N, M, K, nb, use_bias, bi, bj, Tb, Cb, S4, CS);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tables_conn<float>(const double *, int, int, int, int, int, const int16_t *, const int16_t *, cx<float> *, cx<float> *, cx<float> *, cx<float> *, cudaStream_t);
+template cudaError_t launch_tables_conn<double>(const double *, int, int, int, int, int, const int16_t *, const int16_t *, cx<double> *, cx<double> *, cx<double> *, cx<double> *, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_build_tables(const double *params, int N, int M, int K, cx<T> *Wt, cx<T> *b, cx<T> *a, cx<T> *logc,
                                 cx2<T> *X, cx2<T> *XA, cudaStream_t st)

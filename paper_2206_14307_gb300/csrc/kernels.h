@@ -21,12 +21,14 @@ template <typename T>
 cudaError_t launch_ratio(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int mode, double *h1, double *h2,
                          int nsm, cudaStream_t st);
 
-// Bytes of per-chain cache the sampler needs.
+// Bytes of per-chain cache the sampler needs, and the number of chains that
+// run concurrently (the cache is needed for those only).
 template <typename T> size_t sampler_cache_bytes(const DevModel<T> &md);
+template <typename T> int sampler_grid(const DevModel<T> &md, int n_chains, int nsm);
 
 template <typename T>
 cudaError_t launch_sample(const DevModel<T> &md, uint64_t seed, int n_chains, int n_per_chain, int n_skip, int n_burn,
-                          uint64_t *cfg_out, float *acc_out, void *cache, cudaStream_t st);
+                          uint64_t *cfg_out, float *acc_out, void *cache, int nsm, cudaStream_t st);
 
 // Per-CTA scratch of the gradient kernel (U, V rows) and its grid size.
 template <typename T> size_t grad_scratch_bytes(const DevModel<T> &md);
@@ -50,5 +52,9 @@ cudaError_t launch_sr_matvec(const double *O, int64_t n, int64_t P, const double
 template <typename T>
 cudaError_t launch_build_tables(const double *params, int N, int M, int K, cx<T> *Wt, cx<T> *b, cx<T> *a, cx<T> *logc,
                                 cx2<T> *X, cx2<T> *XA, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_tables_conn(const double *params, int N, int M, int K, int nb, int use_bias, const int16_t *bi,
+                               const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, cudaStream_t st);
 
 }  // namespace nnqs
