@@ -179,6 +179,32 @@ int nnqs_energy_grad(const nnqs_model *model, const double *O, const double *elo
 int nnqs_sr_matvec(const nnqs_model *model, const double *O, int64_t n, const double *x,
                    double lambda, double *y, void *stream);
 
+/* Lanczos moments without any device allocation.
+ *
+ * Same result as nnqs_lanczos_moments(model, cfg, n, NULL, NULL, moments_out,
+ * lanczos_out, stream), for callers that cannot allocate device memory at the
+ * point of the call: for example a caller whose device memory is owned up
+ * front by another allocator (a framework's caching pool that holds the whole
+ * budget), or a latency-sensitive loop that must not hit the device-wide
+ * synchronisation that growing the model's workspace with cudaFree/cudaMalloc
+ * implies.  The per-sample h1, h2 and the FP64 partial sums live in one
+ * fixed-size, statically allocated device array of this library
+ * (NNQS_NOALLOC_MAX_SAMPLES samples, about 2 MB), which every GPU that loads
+ * the library holds until the process exits; this call never allocates.
+ * The paper has no counterpart: it is a deployment variant of the call above.
+ *   n must not exceed NNQS_NOALLOC_MAX_SAMPLES (NNQS_EINVAL otherwise).
+ *   moments_out [8], lanczos_out [3]: caller-owned device buffers as above.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture.
+ *   Every call shares the one array and overwrites it completely before it
+ *   reads it back, so nothing carries over between calls; calls whose work
+ *   overlaps on the GPU (different streams or threads at the same time) race
+ *   on it and must be serialised by the caller. */
+#define NNQS_NOALLOC_MAX_SAMPLES 65536
+int nnqs_lanczos_moments_noalloc(nnqs_model *model, const uint64_t *cfg, int64_t n, double *moments_out,
+                                 double *lanczos_out, void *stream);
+
 /* Device status word: NNQS_OK, or NNQS_ERANGE if a kernel produced a
  * non-finite amplitude since the last call.  Synchronises the stream and
  * clears the word. */

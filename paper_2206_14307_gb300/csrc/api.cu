@@ -3,6 +3,7 @@
 // memory of the model, and dispatch to the kernels.
 #include <cstdarg>
 #include <cstdio>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -484,6 +485,69 @@ int nnqs_sr_matvec(const nnqs_model *mc, const double *O, int64_t n, const doubl
         if (rc) return rc;
         cudaError_t e = launch_sr_matvec(O, n, m->P, x, lambda, y, (double *)m->ws, (cudaStream_t)stream);
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "sr_matvec");
+    });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Fixed-size scratch of nnqs_lanczos_moments_noalloc: h1 [max][2], h2 [max][2]
+// and the FP64 partial sums [kNoallocBlocks][6].  In host code the array's
+// name is only a stand-in; its device address is looked up once per device.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoallocBlocks = 64;
+constexpr size_t kNoallocDoubles = (size_t)4 * NNQS_NOALLOC_MAX_SAMPLES + (size_t)kNoallocBlocks * 6;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+namespace {
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[128] = {};  // device address of g_noalloc_scratch, per device
+
+int noalloc_scratch(int device, double **out)
+{
+    if (device < 0 || device >= 128) return fail(NNQS_EUNSUPPORTED, "device ordinal %d out of range", device);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // current device == device
+        if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+        g_noalloc_ptr[device] = (double *)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return NNQS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int nnqs_lanczos_moments_noalloc(nnqs_model *m, const uint64_t *cfg, int64_t n, double *moments, double *lanczos,
+                                 void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n < 0) return fail(NNQS_EINVAL, "n < 0");
+    if (n > NNQS_NOALLOC_MAX_SAMPLES)
+        return fail(NNQS_EINVAL, "n = %lld exceeds the fixed scratch of %d samples", (long long)n,
+                    NNQS_NOALLOC_MAX_SAMPLES);
+    if (n == 0) return NNQS_OK;
+    if (!cfg) return fail(NNQS_EINVAL, "cfg must be non-NULL");
+    return with_device(m, [&]() -> int {
+        double *base = nullptr;
+        const int rc = noalloc_scratch(m->device, &base);
+        if (rc) return rc;
+        double *h1 = base, *h2 = base + 2 * (size_t)NNQS_NOALLOC_MAX_SAMPLES;
+        double *partial = base + 4 * (size_t)NNQS_NOALLOC_MAX_SAMPLES;
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, h1, h2, m->nsm, st)
+                                : launch_ratio(view<float>(m), cfg, n, 1, h1, h2, m->nsm, st);
+        if (e != cudaSuccess) return cuda_fail(e, "lanczos (fixed scratch)");
+        if (moments || lanczos) {
+            e = launch_moments(h1, h2, n, partial, kNoallocBlocks, moments, lanczos, st);
+            if (e != cudaSuccess) return cuda_fail(e, "moments (fixed scratch)");
+        }
+        return NNQS_OK;
     });
 }
 

@@ -27,8 +27,9 @@ ABI_FUNCTIONS = (
     "nnqs_create", "nnqs_destroy", "nnqs_num_params", "nnqs_group_size", "nnqs_set_params",
     "nnqs_set_params_device", "nnqs_sample", "nnqs_log_psi", "nnqs_local_energy",
     "nnqs_lanczos_moments", "nnqs_grad_logpsi", "nnqs_energy_grad", "nnqs_sr_matvec",
-    "nnqs_status", "nnqs_last_error",
+    "nnqs_status", "nnqs_last_error", "nnqs_lanczos_moments_noalloc",
 )
+NOALLOC_MAX_SAMPLES = 65536
 
 
 class nnqs_desc(ctypes.Structure):
@@ -73,6 +74,7 @@ def lib():
             "nnqs_energy_grad": ([P, P, P, i64, P, P], ctypes.c_int),
             "nnqs_sr_matvec": ([P, P, i64, P, d, P, P], ctypes.c_int),
             "nnqs_status": ([P, P], ctypes.c_int),
+            "nnqs_lanczos_moments_noalloc": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -119,6 +121,10 @@ def nnqs_grad_logpsi(h, cfg, n, O, stream=0): return _check(lib().nnqs_grad_logp
 def nnqs_energy_grad(h, O, eloc, n, F, stream=0): return _check(lib().nnqs_energy_grad(h, O, eloc, n, F, stream))
 def nnqs_sr_matvec(h, O, n, x, lam, y, stream=0): return _check(lib().nnqs_sr_matvec(h, O, n, x, lam, y, stream))
 def nnqs_status(h, stream=0): return _check(lib().nnqs_status(h, stream))
+
+
+def nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream=0):
+    return _check(lib().nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream))
 
 
 # ---- torch convenience wrapper ---------------------------------------------------------------
