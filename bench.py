@@ -45,9 +45,10 @@ PARAM_STD, PARAM_SEED = 0.01, 2206
 WORKLOAD = "6x6 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=72), 288 ops + spin inversion; 1024 chains x 16 samples"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
 FLOPS_PER_ELEMENT = 28   # one connected factor p e^D + (1-p) e^-D and its running product
-# DRAM bytes per k_ratio launch of this workload from the ncu capture summarised
-# in profiles/k_ratio_6x6.txt (None until captured for the current kernel)
-K_RATIO_TRAFFIC = None
+# DRAM bytes (read + write) per E_loc launch of this workload: the ncu capture of
+# profiles/k_eloc_k_sample_6x6_small.md measured 0.42 MB for 2048 samples; the
+# traffic grows with the samples, so a 16384-sample launch moves 8x that.
+K_RATIO_TRAFFIC = 8 * 0.418304e6
 
 
 def bonds(L):
@@ -307,7 +308,7 @@ def main():
                    "precision": "FP32 (exact exponent tracking)", "l2": "flushed (512 MB write) before every step"},
         "eloc_samples_per_s": world * N_SAMPLES / (ms / 1e3),
         "acceptance": res["acc"], "E_loc_mean_per_site": res["e_mean"],
-        "roofline": {"kernel": "k_ratio (E_loc connected-amplitude engine)", "bound": "alu",
+        "roofline": {"kernel": "k_eloc (E_loc connected-amplitude engine)", "bound": "alu",
                      "achieved": eloc_ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": eloc_ach / FP32_PEAK_TFLOPS, "traffic": K_RATIO_TRAFFIC,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",

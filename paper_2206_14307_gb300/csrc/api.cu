@@ -119,7 +119,7 @@ struct nnqs_model {
     void *chi = nullptr;
     double *params = nullptr;
     void *Wt = nullptr, *b = nullptr, *a = nullptr, *logc = nullptr, *X = nullptr, *XA = nullptr;
-    void *Tb = nullptr, *Cb = nullptr, *S4 = nullptr, *CS = nullptr;
+    void *Tb = nullptr, *Cb = nullptr, *S4 = nullptr, *CS = nullptr, *ES = nullptr;
     uint16_t *bperm = nullptr;
     int *status = nullptr;
     void *ws = nullptr;
@@ -132,6 +132,7 @@ template <typename T> DevModel<T> view(const nnqs_model *m)
 {
     DevModel<T> v;
     v.L = m->d.L; v.N = m->N; v.K = m->d.K; v.M = m->d.M; v.G = m->G; v.nsign = m->nsign;
+    v.Mp = conn_mpad(m->d.M);
     v.use_bias = m->d.use_bias; v.nbonds = m->nbonds; v.nwords = m->nwords; v.chiP = m->d.spin_inversion;
     v.J1 = (T)m->d.J1; v.J2 = (T)m->d.J2;
     v.perm = m->perm; v.chi = (const T *)m->chi;
@@ -140,6 +141,7 @@ template <typename T> DevModel<T> view(const nnqs_model *m)
     v.bond_i = m->bi; v.bond_j = m->bj; v.bond_t = m->bt;
     v.Tb = (const cx<T> *)m->Tb; v.Cb = (const cx<T> *)m->Cb; v.S4 = (const cx<T> *)m->S4; v.CS = (const cx<T> *)m->CS;
     v.bperm = m->bperm;
+    v.ES = (const sc<T> *)m->ES;
     v.status = m->status;
     return v;
 }
@@ -240,10 +242,12 @@ int nnqs_create(const nnqs_desc *desc, nnqs_model **out)
     ALLOC(m->logc, K * 2 * ts);
     ALLOC(m->X, K * N * M * 4 * ts);
     ALLOC(m->XA, K * N * 4 * ts);
-    ALLOC(m->Tb, K * 2 * bi.size() * M * 2 * ts);
+    const size_t Mp = (size_t)conn_mpad(d.M);
+    ALLOC(m->Tb, K * 2 * bi.size() * Mp * 2 * ts);
     ALLOC(m->Cb, K * bi.size() * 2 * ts);
-    ALLOC(m->S4, K * 2 * N * M * 2 * ts);
+    ALLOC(m->S4, K * 2 * N * Mp * 2 * ts);
     ALLOC(m->CS, K * N * 2 * ts);
+    ALLOC(m->ES, K * 2 * N * (m->fp64 ? sizeof(sc<double>) : sizeof(sc<float>)));
     ALLOC(m->bperm, (size_t)m->G * bi.size() * sizeof(uint16_t));
     ALLOC(m->status, sizeof(int));
 #undef ALLOC
@@ -288,7 +292,7 @@ int nnqs_destroy(nnqs_model *m)
     if (!m) return NNQS_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {m->perm, m->bi, m->bj, m->bt, m->chi, m->params, m->Wt, m->b, m->a, m->logc, m->X, m->XA,
-                    m->Tb, m->Cb, m->S4, m->CS, m->bperm, m->status, m->ws};
+                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->ws};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -320,11 +324,11 @@ int nnqs_set_params_device(nnqs_model *m, const double *params, int64_t P, void 
         if (m->fp64)
             e = launch_tables_conn<double>(m->params, m->N, m->d.M, m->d.K, m->nbonds, m->d.use_bias, m->bi, m->bj,
                                            (cx<double> *)m->Tb, (cx<double> *)m->Cb, (cx<double> *)m->S4,
-                                           (cx<double> *)m->CS, st);
+                                           (cx<double> *)m->CS, (sc<double> *)m->ES, st);
         else
             e = launch_tables_conn<float>(m->params, m->N, m->d.M, m->d.K, m->nbonds, m->d.use_bias, m->bi, m->bj,
                                           (cx<float> *)m->Tb, (cx<float> *)m->Cb, (cx<float> *)m->S4,
-                                          (cx<float> *)m->CS, st);
+                                          (cx<float> *)m->CS, (sc<float> *)m->ES, st);
         if (e != cudaSuccess) return cuda_fail(e, "build connection tables");
         return NNQS_OK;
     });

@@ -29,9 +29,11 @@ template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
 template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return cx<T>{a.x + b.x, a.y + b.y}; }
 template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return cx<T>{a.x - b.x, a.y - b.y}; }
 template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return cx<T>{a.x * s, a.y * s}; }
+template <typename T> __device__ __forceinline__ T recip(T x) { return T(1) / x; }
+template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 template <typename T> __device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b)
 {
-    T d = T(1) / (b.x * b.x + b.y * b.y);
+    T d = recip<T>(b.x * b.x + b.y * b.y);
     return cx<T>{(a.x * b.x + a.y * b.y) * d, (a.y * b.x - a.x * b.y) * d};
 }
 
@@ -181,8 +183,17 @@ __device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 // ---------------------------------------------------------------------------
 // Device view of a model (passed by value to kernels)
 // ---------------------------------------------------------------------------
+// Row stride of the connected-configuration tables: M padded to the
+// (lanes per row) x (units per lane) tiling of the kernel variant, with neutral
+// entries (T = 0, e^{+-4W} = 1) past M so that the inner loops need no bound.
+__host__ __device__ __forceinline__ int conn_mpad(int M)
+{
+    return M <= 16 ? 16 : M <= 32 ? 32 : M <= 72 ? 72 : M <= 128 ? 128 : M <= 256 ? 256 : M <= 416 ? 416 : 512;
+}
+
 template <typename T> struct DevModel {
     int L, N, K, M, G, nsign, use_bias, nbonds, nwords, chiP;
+    int Mp;                 // row stride of Tb and S4 (conn_mpad(M))
     T J1, J2;
     const uint8_t *perm;    // [G][N]   image of site i under g
     const T *chi;           // [G]      +-1
@@ -195,11 +206,12 @@ template <typename T> struct DevModel {
     // connected-configuration tables (bond b' = (a, b) of the bond list,
     // D0_m = -2 (W_ma - W_mb) the change of theta_m when s_a = +1, s_b = -1
     // are exchanged):
-    const cx<T> *Tb;        // [K][2][4N][M]  exp(+2 D0_m) - 1, exp(-2 D0_m) - 1
+    const cx<T> *Tb;        // [K][2][4N][Mp] exp(+2 D0_m) - 1, exp(-2 D0_m) - 1
     const cx<T> *Cb;        // [K][4N]        -2 (a_a - a_b) + 2 sum_m (W_ma - W_mb)
-    const cx<T> *S4;        // [K][2][N][M]   exp(-4 W_mk), exp(+4 W_mk)
+    const cx<T> *S4;        // [K][2][N][Mp]  exp(-4 W_mk), exp(+4 W_mk)
     const cx<T> *CS;        // [K][N]         sum_m W_mk
     const uint16_t *bperm;  // [G][4N]        image bond of b under g | (orientation flip << 15)
+    const sc<T> *ES;        // [K][2][N]      exp(+-Cs_k), Cs_k = 2 sum_m W_mk - 2 a_k (site prefactors)
     const int16_t *bond_i;  // [4N]
     const int16_t *bond_j;  // [4N]
     const uint8_t *bond_t;  // [4N] 1 = J1, 2 = J2

@@ -49,7 +49,7 @@ __device__ __forceinline__ bool candidate2(const DevModel<T> &md, int mode, int 
     if (mode == 0) {
         const int i = md.bond_i[q], j = md.bond_j[q];
         if (s8[i] == s8[j]) return false;
-        e.code = ecode(kOneBond, q, 0);
+        e.code = ecode(kOneBond, q, s8[i] > 0);
         e.c1 = T(0.5) * bondJ(md, q);
         e.c2 = T(0);
         return true;
@@ -69,7 +69,7 @@ __device__ __forceinline__ bool candidate2(const DevModel<T> &md, int mode, int 
             const int sj2 = (j == i1) ? s8[j1] : (j == j1) ? s8[i1] : sj;
             d += T(0.25) * bondJ(md, b) * T(si2 * sj2 - si * sj);
         }
-        e.code = ecode(kOneBond, b1, 0);
+        e.code = ecode(kOneBond, b1, s8[i1] > 0);
         e.c1 = T(0.5) * J1b;
         e.c2 = T(0.5) * J1b * d;
         return true;
@@ -104,101 +104,119 @@ template <typename T> struct Dec {
     cx<T> E;         // prefactor exponent for sign +1 (sign -1 uses -E)
 };
 
-template <typename T>
+template <typename T, bool WITH_E>
 __device__ __forceinline__ Dec<T> decode(const DevModel<T> &md, uint32_t code, int r, int g, const int8_t *s8)
 {
     Dec<T> d;
-    const int nb = md.nbonds, M = md.M, N = md.N;
+    const int nb = md.nbonds, Mp = md.Mp, N = md.N;
     d.type = (int)(code >> 30);
     const int i0 = code & 0x7fff, i1 = (code >> 15) & 0x7fff;
-    const size_t rb = (size_t)r * 2 * nb * M;   // Tb block of RBM r
+    const int rb = r * 2 * nb * Mp;   // Tb block of RBM r
+    d.E = cx<T>{T(0), T(0)};
     if (d.type != kSitePair) {
         const uint16_t bp0 = md.bperm[(size_t)g * nb + i0];
         const int bb0 = bp0 & 0x7fff;
-        const int s0 = s8[md.bond_i[i0]] * ((bp0 >> 15) ? -1 : 1);
-        d.o0 = (int)(rb + ((size_t)(s0 > 0 ? 0 : 1) * nb + bb0) * M);
-        d.d0 = s0 > 0 ? nb * M : -nb * M;
-        const cx<T> c0 = md.Cb[(size_t)r * nb + bb0];
-        d.E = cx<T>{T(s0) * c0.x, T(s0) * c0.y};
+        const int si0 = d.type == kOneBond ? (i1 ? 1 : -1) : s8[md.bond_i[i0]];
+        const int s0 = si0 * ((bp0 >> 15) ? -1 : 1);
+        d.o0 = rb + ((s0 > 0 ? 0 : 1) * nb + bb0) * Mp;
+        d.d0 = s0 > 0 ? nb * Mp : -nb * Mp;
+        if (WITH_E) {
+            const cx<T> c0 = md.Cb[(size_t)r * nb + bb0];
+            d.E = cx<T>{T(s0) * c0.x, T(s0) * c0.y};
+        }
         d.o1 = 0; d.d1 = 0;
         if (d.type == kTwoBonds) {
             const uint16_t bp1 = md.bperm[(size_t)g * nb + i1];
             const int bb1 = bp1 & 0x7fff;
             const int s1 = s8[md.bond_i[i1]] * ((bp1 >> 15) ? -1 : 1);
-            d.o1 = (int)(rb + ((size_t)(s1 > 0 ? 0 : 1) * nb + bb1) * M);
-            d.d1 = s1 > 0 ? nb * M : -nb * M;
-            const cx<T> c1 = md.Cb[(size_t)r * nb + bb1];
-            d.E.x += T(s1) * c1.x;
-            d.E.y += T(s1) * c1.y;
+            d.o1 = rb + ((s1 > 0 ? 0 : 1) * nb + bb1) * Mp;
+            d.d1 = s1 > 0 ? nb * Mp : -nb * Mp;
+            if (WITH_E) {
+                const cx<T> c1 = md.Cb[(size_t)r * nb + bb1];
+                d.E.x += T(s1) * c1.x;
+                d.E.y += T(s1) * c1.y;
+            }
         }
     } else {
         // sites u (spin s_u) and v (spin -s_u) flipped
         const int ku = md.perm[(size_t)g * N + i0], kv = md.perm[(size_t)g * N + i1];
         const int su = s8[i0];
-        const size_t rs = (size_t)r * 2 * N * M;
-        d.o0 = (int)(rs + ((size_t)(su > 0 ? 0 : 1) * N + ku) * M);
-        d.d0 = su > 0 ? N * M : -N * M;
-        d.o1 = (int)(rs + ((size_t)(su > 0 ? 1 : 0) * N + kv) * M);
-        d.d1 = su > 0 ? -N * M : N * M;
-        cx<T> ca{T(0), T(0)};
-        if (md.use_bias) {
-            const cx<T> au = md.avec[(size_t)r * N + ku], av = md.avec[(size_t)r * N + kv];
-            ca = cx<T>{T(-2) * (au.x - av.x), T(-2) * (au.y - av.y)};
+        const int rs = r * 2 * N * Mp;
+        d.o0 = rs + ((su > 0 ? 0 : 1) * N + ku) * Mp;
+        d.d0 = su > 0 ? N * Mp : -N * Mp;
+        d.o1 = rs + ((su > 0 ? 1 : 0) * N + kv) * Mp;
+        d.d1 = su > 0 ? -N * Mp : N * Mp;
+        if (WITH_E) {
+            cx<T> ca{T(0), T(0)};
+            if (md.use_bias) {
+                const cx<T> au = md.avec[(size_t)r * N + ku], av = md.avec[(size_t)r * N + kv];
+                ca = cx<T>{T(-2) * (au.x - av.x), T(-2) * (au.y - av.y)};
+            }
+            const cx<T> cu = md.CS[(size_t)r * N + ku], cv = md.CS[(size_t)r * N + kv];
+            const cx<T> c{ca.x + T(2) * (cu.x - cv.x), ca.y + T(2) * (cu.y - cv.y)};
+            d.E = cx<T>{T(su) * c.x, T(su) * c.y};
         }
-        const cx<T> cu = md.CS[(size_t)r * N + ku], cv = md.CS[(size_t)r * N + kv];
-        const cx<T> c{ca.x + T(2) * (cu.x - cv.x), ca.y + T(2) * (cu.y - cv.y)};
-        d.E = cx<T>{T(su) * c.x, T(su) * c.y};
     }
     return d;
 }
 
 // prod over the lane's hidden units m = gl + GL j of (1 + p_m T_m) for one
-// entry and one sign
-template <typename T, int GL, int MPL>
+// entry and one sign.  The tables are padded to GL * MPL with neutral entries
+// (and p_m = 0 past M), so no bound check is needed.
+template <typename T, int GL, int MPL, bool ONLY1>
 __device__ __forceinline__ cx<T> entry_partial(const DevModel<T> &md, const Dec<T> &d, int sg, const cx<T> (&p)[MPL],
                                                int gl)
 {
-    const int M = md.M;
-    const int o0 = sg ? d.o0 + d.d0 : d.o0;
-    const int o1 = sg ? d.o1 + d.d1 : d.o1;
+    const int o0 = (sg ? d.o0 + d.d0 : d.o0) + gl;
+    const int o1 = (sg ? d.o1 + d.d1 : d.o1) + gl;
     cx<T> pr{T(1), T(0)};
-    if (d.type == kOneBond) {
+    if (ONLY1 || d.type == kOneBond) {
+        const cx<T> *__restrict__ tb = md.Tb + o0;
 #pragma unroll
         for (int j = 0; j < MPL; ++j) {
-            const int m = gl + GL * j;
-            if (m < M) {
-                const cx<T> t = md.Tb[o0 + m];
-                const cx<T> f{T(1) + p[j].x * t.x - p[j].y * t.y, p[j].x * t.y + p[j].y * t.x};
-                pr = cmul(pr, f);
-            }
+            const cx<T> t = tb[GL * j];
+            const cx<T> f{T(1) + p[j].x * t.x - p[j].y * t.y, p[j].x * t.y + p[j].y * t.x};
+            pr = cmul(pr, f);
         }
-    } else {
-        const cx<T> *tab = d.type == kTwoBonds ? md.Tb : md.S4;
+    } else if constexpr (!ONLY1) {
+        const cx<T> *__restrict__ tab = d.type == kTwoBonds ? md.Tb : md.S4;
+        const cx<T> *__restrict__ t0p = tab + o0;
+        const cx<T> *__restrict__ t1p = tab + o1;
 #pragma unroll
         for (int j = 0; j < MPL; ++j) {
-            const int m = gl + GL * j;
-            if (m < M) {
-                const cx<T> t0 = tab[o0 + m], t1 = tab[o1 + m];
-                cx<T> t;
-                if (d.type == kTwoBonds) {
-                    t = cadd(cadd(t0, t1), cmul(t0, t1));  // (1 + t0)(1 + t1) - 1
-                } else {
-                    const cx<T> x = cmul(t0, t1);
-                    t = cx<T>{x.x - T(1), x.y};
-                }
-                const cx<T> f{T(1) + p[j].x * t.x - p[j].y * t.y, p[j].x * t.y + p[j].y * t.x};
-                pr = cmul(pr, f);
+            const cx<T> t0 = t0p[GL * j], t1 = t1p[GL * j];
+            cx<T> t;
+            if (d.type == kTwoBonds) {
+                t = cadd(cadd(t0, t1), cmul(t0, t1));  // (1 + t0)(1 + t1) - 1
+            } else {
+                const cx<T> x = cmul(t0, t1);
+                t = cx<T>{x.x - T(1), x.y};
             }
+            const cx<T> f{T(1) + p[j].x * t.x - p[j].y * t.y, p[j].x * t.y + p[j].y * t.x};
+            pr = cmul(pr, f);
         }
     }
     return pr;
 }
 
-template <typename T, int GL, int MPL>
-__global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
-                                                   int mode, int chunk, double *__restrict__ h1_out,
-                                                   double *__restrict__ h2_out)
+// mantissa / exponent split of a partial product, skipped in the common range
+template <typename T> __device__ __forceinline__ void split(cx<T> pr, T &x, T &y, int &e)
 {
+    const T mx = fmax(fabs(pr.x), fabs(pr.y));
+    if (mx > T(9.094947017729282e-13) && mx < T(1.099511627776e12)) {  // 2^-40 .. 2^40
+        x = pr.x; y = pr.y; e = 0;
+    } else {
+        e = expo<T>(pr.x, pr.y);
+        const T scl = pow2i<T>(-e);
+        x = pr.x * scl; y = pr.y * scl;
+    }
+}
+
+template <typename T, int GL, int MPL, int MODE>
+__global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
+                                                   int chunk, double *__restrict__ h1_out, double *__restrict__ h2_out)
+{
+    constexpr int mode = MODE;
     constexpr int NG = 32 / GL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T s_sm[kMaxN];
@@ -214,10 +232,11 @@ __global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_
 
     Entry2<T> *ent = reinterpret_cast<Entry2<T> *>(smem_raw);
     sc<T> *acc = reinterpret_cast<sc<T> *>(smem_raw + sizeof(Entry2<T>) * chunk);  // [kWarps][chunk]
-    // transpose tiles of the one-row-per-warp variant: [kWarps][8][33]
+    // transpose tiles of the partial products: [kWarps][TQ][33], TQ = GL (8 for GL = 32)
+    constexpr int TQ = GL < 32 ? GL : 8;
     T *tx = reinterpret_cast<T *>(smem_raw + (sizeof(Entry2<T>) + kWarps * sizeof(sc<T>)) * chunk);
-    T *ty = tx + (GL == 32 ? kWarps * 8 * 33 : 0);
-    int *te = reinterpret_cast<int *>(ty + (GL == 32 ? kWarps * 8 * 33 : 0));
+    T *ty = tx + kWarps * TQ * 33;
+    int *te = reinterpret_cast<int *>(ty + kWarps * TQ * 33);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / GL, gl = lane % GL;
@@ -369,46 +388,54 @@ __global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_
 
                 // ---- entries, GL at a time ----
                 if constexpr (GL < 32) {
+                    // Rolled loop over the GL entries of a batch: each lane writes its
+                    // partial product (over its hidden units) of entry e0 + q into the
+                    // group's tile; lane gl then multiplies the GL partials of entry
+                    // e0 + gl.  Tile [warp][q][lane], row stride 33 words.
+                    T *bx = tx + warp * GL * 33, *by = ty + warp * GL * 33;
+                    int *be = te + warp * GL * 33;
                     for (int e0 = 0; e0 < ne; e0 += GL) {
                         sc<T> mine{T(0), T(0), 0};  // lane gl: contribution of entry e0 + gl
 #pragma unroll
                         for (int sg = 0; sg < 2; ++sg) {
                             if (sg >= md.nsign) break;
-                            cx<T> v[GL];
-                            int ve[GL];
-                            cx<T> myE{T(0), T(0)};
-#pragma unroll
+#pragma unroll 1
                             for (int q = 0; q < GL; ++q) {
                                 const int e = e0 + q;
                                 cx<T> pr{T(1), T(0)};
                                 if (e < ne) {
-                                    const Dec<T> d = decode(md, ent[e].code, r, g, s8);
-                                    if (q == gl) myE = sg ? cx<T>{-d.E.x, -d.E.y} : d.E;
-                                    pr = entry_partial<T, GL, MPL>(md, d, sg, p[sg], gl);
+                                    const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, s8);
+                                    pr = entry_partial<T, GL, MPL, MODE == 0>(md, d, sg, p[sg], gl);
                                 }
-                                const int ex = expo<T>(pr.x, pr.y);
-                                const T scl = pow2i<T>(-ex);
-                                v[q] = cx<T>{pr.x * scl, pr.y * scl};
-                                ve[q] = ex;
+                                T sx, sy;
+                                int ex;
+                                split(pr, sx, sy, ex);
+                                bx[q * 33 + lane] = sx;
+                                by[q * 33 + lane] = sy;
+                                be[q * 33 + lane] = ex;
                             }
-                            // butterfly reduce-scatter: lane gl ends with entry gl
+                            __syncwarp();
+                            cx<T> pr{T(1), T(0)};
+                            int pe = 0;
 #pragma unroll
-                            for (int o = GL / 2; o > 0; o >>= 1) {
-                                const bool hi = (gl & o) != 0;
-#pragma unroll
-                                for (int k = 0; k < o; ++k) {
-                                    const cx<T> keep = hi ? v[k + o] : v[k];
-                                    const cx<T> send = hi ? v[k] : v[k + o];
-                                    const int keepe = hi ? ve[k + o] : ve[k];
-                                    const int sende = hi ? ve[k] : ve[k + o];
-                                    const cx<T> recv{shfl_x(send.x, o), shfl_x(send.y, o)};
-                                    const int recve = __shfl_xor_sync(0xffffffffu, sende, o);
-                                    v[k] = cmul(keep, recv);
-                                    ve[k] = keepe + recve;
+                            for (int k = 0; k < GL; ++k) {
+                                const int idx = gl * 33 + grp * GL + k;
+                                pr = cmul(pr, cx<T>{bx[idx], by[idx]});
+                                pe += be[idx];
+                                if ((k & 1) == 1) {   // values are below 2^40: renormalise every two
+                                    T sx, sy;
+                                    int ex;
+                                    split(pr, sx, sy, ex);
+                                    pr = cx<T>{sx, sy};
+                                    pe += ex;
                                 }
                             }
-                            if (e0 + gl < ne && active) {
-                                const sc<T> c = sc_mul(sc_norm(sc<T>{v[0].x, v[0].y, ve[0]}), sc_exp(myE));
+                            __syncwarp();
+                            const int e = e0 + gl;
+                            if (e < ne && active) {
+                                const Dec<T> d = decode<T, true>(md, ent[e].code, r, g, s8);
+                                const cx<T> E = sg ? cx<T>{-d.E.x, -d.E.y} : d.E;
+                                const sc<T> c = sc_mul(sc_norm(sc<T>{pr.x, pr.y, pe}), sc_exp(E));
                                 mine = sc_add(mine, sc_mul(c, term[sg]));
                             }
                         }
@@ -425,8 +452,8 @@ __global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_
                     // One row per warp: transpose the lanes' partial products of 8
                     // entries through shared memory; lane (e, part) multiplies 8 of
                     // the 32 partials of entry e, two shuffle stages combine the parts.
-                    T *bx = tx + warp * 8 * 33, *by = ty + warp * 8 * 33;
-                    int *be = te + warp * 8 * 33;
+                    T *bx = tx + warp * TQ * 33, *by = ty + warp * TQ * 33;
+                    int *be = te + warp * TQ * 33;
                     const int el = lane & 7, part = lane >> 3;
                     for (int e0 = 0; e0 < ne; e0 += 8) {
 #pragma unroll
@@ -437,13 +464,14 @@ __global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_
                                 const int e = e0 + q;
                                 cx<T> pr{T(1), T(0)};
                                 if (e < ne) {
-                                    const Dec<T> d = decode(md, ent[e].code, r, g, s8);
-                                    pr = entry_partial<T, GL, MPL>(md, d, sg, p[sg], gl);
+                                    const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, s8);
+                                    pr = entry_partial<T, GL, MPL, MODE == 0>(md, d, sg, p[sg], gl);
                                 }
-                                const int ex = expo<T>(pr.x, pr.y);
-                                const T scl = pow2i<T>(-ex);
-                                bx[q * 33 + lane] = pr.x * scl;
-                                by[q * 33 + lane] = pr.y * scl;
+                                T sx, sy;
+                                int ex;
+                                split(pr, sx, sy, ex);
+                                bx[q * 33 + lane] = sx;
+                                by[q * 33 + lane] = sy;
                                 be[q * 33 + lane] = ex;
                             }
                             __syncwarp();
@@ -454,6 +482,13 @@ __global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_
                                 const int idx = el * 33 + part * 8 + l;
                                 pr = cmul(pr, cx<T>{bx[idx], by[idx]});
                                 pe += be[idx];
+                                if ((l & 1) == 1) {   // values are below 2^40: renormalise every two
+                                    T sx, sy;
+                                    int ex;
+                                    split(pr, sx, sy, ex);
+                                    pr = cx<T>{sx, sy};
+                                    pe += ex;
+                                }
                             }
                             __syncwarp();
 #pragma unroll
@@ -461,10 +496,15 @@ __global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_
                                 const cx<T> w{shfl_x(pr.x, o), shfl_x(pr.y, o)};
                                 pe += __shfl_xor_sync(0xffffffffu, pe, o);
                                 pr = cmul(pr, w);
+                                T sx, sy;
+                                int ex;
+                                split(pr, sx, sy, ex);
+                                pr = cx<T>{sx, sy};
+                                pe += ex;
                             }
                             const int e = e0 + el;
                             if (part == 0 && e < ne && active) {
-                                const Dec<T> d = decode(md, ent[e].code, r, g, s8);
+                                const Dec<T> d = decode<T, true>(md, ent[e].code, r, g, s8);
                                 const cx<T> E = sg ? cx<T>{-d.E.x, -d.E.y} : d.E;
                                 const sc<T> c = sc_mul(sc_norm(sc<T>{pr.x, pr.y, pe}), sc_exp(E));
                                 acc[warp * chunk + e] = sc_add(acc[warp * chunk + e], sc_mul(c, term[sg]));
@@ -541,22 +581,24 @@ __global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_
 // own translation unit (k_eloc_<type>_<GL>_<MPL>.cu) so they compile in parallel.
 template <typename T, int GL> size_t eloc_smem(int chunk)
 {
-    const size_t tiles = GL == 32 ? (size_t)kWarps * 8 * 33 * (2 * sizeof(T) + sizeof(int)) : 0;
+    const size_t tiles = (size_t)kWarps * (GL < 32 ? GL : 8) * 33 * (2 * sizeof(T) + sizeof(int));
     return (sizeof(Entry2<T>) + kWarps * sizeof(sc<T>)) * (size_t)chunk + tiles;
 }
 
-template <typename T, int GL, int MPL>
-cudaError_t launch_eloc_variant(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int mode, int chunk, double *h1,
-                                double *h2, int nsm, cudaStream_t st)
+template <typename T, int GL, int MPL, int MODE>
+cudaError_t launch_eloc_mode(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int chunk, double *h1, double *h2,
+                             int nsm, cudaStream_t st)
 {
     const size_t smem = eloc_smem<T, GL>(chunk);
-    cudaError_t err = cudaFuncSetAttribute(k_eloc<T, GL, MPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_eloc<T, GL, MPL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 0;
-    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_eloc<T, GL, MPL>, kThreads, smem);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_eloc<T, GL, MPL, MODE>, kThreads, smem);
     if (err != cudaSuccess) return err;
     const int64_t grid = (int64_t)(per > 0 ? per : 1) * nsm;
     const int gsz = (int)(n < grid ? n : grid);
-    k_eloc<T, GL, MPL><<<gsz, kThreads, smem, st>>>(md, cfg, n, mode, chunk, h1, h2);
+    k_eloc<T, GL, MPL, MODE><<<gsz, kThreads, smem, st>>>(md, cfg, n, chunk, h1, h2);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,8 @@
+// float instantiation of the connected-configuration engine: GL = 8, MPL = 9,
+// all flip-set kinds (Lanczos).
+#include "k_eloc.cuh"
+
+namespace nnqs {
+template cudaError_t launch_eloc_mode<float, 8, 9, 1>(const DevModel<float> &, const uint64_t *, int64_t, int,
+                                                             double *, double *, int, cudaStream_t);
+}  // namespace nnqs

@@ -1,0 +1,8 @@
+// double instantiation of the connected-configuration engine: GL = 32, MPL = 13,
+// all flip-set kinds (Lanczos).
+#include "k_eloc.cuh"
+
+namespace nnqs {
+template cudaError_t launch_eloc_mode<double, 32, 13, 1>(const DevModel<double> &, const uint64_t *, int64_t, int,
+                                                             double *, double *, int, cudaStream_t);
+}  // namespace nnqs

@@ -239,38 +239,55 @@ __device__ __forceinline__ void cexpm1(double x, double y, double &re, double &i
     im = exp(x) * sy;
 }
 
+// exp(z) as a scaled number: mantissa * 2^e with |mantissa| in [1, 2)
+template <typename T> __device__ __forceinline__ sc<T> exp_scaled(double x, double y)
+{
+    const double t = x * 1.4426950408889634;
+    const double k = floor(t);
+    const double m = exp2(t - k);
+    double s, c;
+    sincos(y, &s, &c);
+    return sc<T>{(T)(m * c), (T)(m * s), (int)k};
+}
+
 template <typename T>
 __global__ void k_tables_conn(const double *__restrict__ par, int N, int M, int K, int nb, int use_bias,
                               const int16_t *__restrict__ bi, const int16_t *__restrict__ bj, cx<T> *Tb, cx<T> *Cb,
-                              cx<T> *S4, cx<T> *CS)
+                              cx<T> *S4, cx<T> *CS, sc<T> *ES)
 {
     const int64_t P1 = 1 + N + M + (int64_t)M * N;
-    const int64_t n1 = (int64_t)K * nb * M, n2 = (int64_t)K * N * M, n3 = (int64_t)K * nb, n4 = (int64_t)K * N;
+    const int Mp = conn_mpad(M);
+    const int64_t n1 = (int64_t)K * nb * Mp, n2 = (int64_t)K * N * Mp, n3 = (int64_t)K * nb, n4 = (int64_t)K * N;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n1 + n2 + n3 + n4;
          q += (int64_t)gridDim.x * blockDim.x) {
         if (q < n1) {
-            const int r = (int)(q / ((int64_t)nb * M));
-            const int64_t rem = q - (int64_t)r * nb * M;
-            const int b = (int)(rem / M), m = (int)(rem - (int64_t)b * M);
-            const double *W = par + 2 * (r * P1 + 1 + N + M + (int64_t)m * N);
-            const int a = bi[b], c = bj[b];
-            const double zx = -4.0 * (W[2 * a] - W[2 * c]), zy = -4.0 * (W[2 * a + 1] - W[2 * c + 1]);
-            double px, py, mx, my;
-            cexpm1(zx, zy, px, py);
-            cexpm1(-zx, -zy, mx, my);
-            Tb[(((size_t)r * 2 + 0) * nb + b) * M + m] = cx<T>{(T)px, (T)py};
-            Tb[(((size_t)r * 2 + 1) * nb + b) * M + m] = cx<T>{(T)mx, (T)my};
+            const int r = (int)(q / ((int64_t)nb * Mp));
+            const int64_t rem = q - (int64_t)r * nb * Mp;
+            const int b = (int)(rem / Mp), m = (int)(rem - (int64_t)b * Mp);
+            double px = 0, py = 0, mx = 0, my = 0;  // padding: T = 0
+            if (m < M) {
+                const double *W = par + 2 * (r * P1 + 1 + N + M + (int64_t)m * N);
+                const int a = bi[b], c = bj[b];
+                const double zx = -4.0 * (W[2 * a] - W[2 * c]), zy = -4.0 * (W[2 * a + 1] - W[2 * c + 1]);
+                cexpm1(zx, zy, px, py);
+                cexpm1(-zx, -zy, mx, my);
+            }
+            Tb[(((size_t)r * 2 + 0) * nb + b) * Mp + m] = cx<T>{(T)px, (T)py};
+            Tb[(((size_t)r * 2 + 1) * nb + b) * Mp + m] = cx<T>{(T)mx, (T)my};
         } else if (q < n1 + n2) {
             const int64_t u = q - n1;
-            const int r = (int)(u / ((int64_t)N * M));
-            const int64_t rem = u - (int64_t)r * N * M;
-            const int k = (int)(rem / M), m = (int)(rem - (int64_t)k * M);
-            const double *W = par + 2 * (r * P1 + 1 + N + M + (int64_t)m * N + k);
-            double s, c;
-            sincos(4.0 * W[1], &s, &c);
-            const double em = exp(-4.0 * W[0]), ep = exp(4.0 * W[0]);
-            S4[(((size_t)r * 2 + 0) * N + k) * M + m] = cx<T>{(T)(em * c), (T)(-em * s)};
-            S4[(((size_t)r * 2 + 1) * N + k) * M + m] = cx<T>{(T)(ep * c), (T)(ep * s)};
+            const int r = (int)(u / ((int64_t)N * Mp));
+            const int64_t rem = u - (int64_t)r * N * Mp;
+            const int k = (int)(rem / Mp), m = (int)(rem - (int64_t)k * Mp);
+            double s = 0, c = 1, em = 1, ep = 1;  // padding: exp(+-4W) = 1
+            if (m < M) {
+                const double *W = par + 2 * (r * P1 + 1 + N + M + (int64_t)m * N + k);
+                sincos(4.0 * W[1], &s, &c);
+                em = exp(-4.0 * W[0]);
+                ep = exp(4.0 * W[0]);
+            }
+            S4[(((size_t)r * 2 + 0) * N + k) * Mp + m] = cx<T>{(T)(em * c), (T)(-em * s)};
+            S4[(((size_t)r * 2 + 1) * N + k) * Mp + m] = cx<T>{(T)(ep * c), (T)(ep * s)};
         } else if (q < n1 + n2 + n3) {
             const int64_t u = q - n1 - n2;
             const int r = (int)(u / nb), b = (int)(u - (int64_t)r * nb);
@@ -299,20 +316,29 @@ __global__ void k_tables_conn(const double *__restrict__ par, int N, int M, int 
                 sy += W[1];
             }
             CS[(size_t)r * N + k] = cx<T>{(T)sx, (T)sy};
+            // site prefactor exponent Cs_k = 2 sum_m W_mk - 2 a_k
+            double cx_ = 2.0 * sx, cy_ = 2.0 * sy;
+            if (use_bias) {
+                cx_ -= 2.0 * base[2 * (1 + k)];
+                cy_ -= 2.0 * base[2 * (1 + k) + 1];
+            }
+            ES[((size_t)r * 2 + 0) * N + k] = exp_scaled<T>(cx_, cy_);
+            ES[((size_t)r * 2 + 1) * N + k] = exp_scaled<T>(-cx_, -cy_);
         }
     }
 }
 
 template <typename T>
 cudaError_t launch_tables_conn(const double *params, int N, int M, int K, int nb, int use_bias, const int16_t *bi,
-                               const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, cudaStream_t st)
+                               const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, sc<T> *ES,
+                               cudaStream_t st)
 {
-    k_tables_conn<T><<<2048, 256, 0, st>>>(params, N, M, K, nb, use_bias, bi, bj, Tb, Cb, S4, CS);
+    k_tables_conn<T><<<2048, 256, 0, st>>>(params, N, M, K, nb, use_bias, bi, bj, Tb, Cb, S4, CS, ES);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_tables_conn<float>(const double *, int, int, int, int, int, const int16_t *, const int16_t *, cx<float> *, cx<float> *, cx<float> *, cx<float> *, cudaStream_t);
-template cudaError_t launch_tables_conn<double>(const double *, int, int, int, int, int, const int16_t *, const int16_t *, cx<double> *, cx<double> *, cx<double> *, cx<double> *, cudaStream_t);
+template cudaError_t launch_tables_conn<float>(const double *, int, int, int, int, int, const int16_t *, const int16_t *, cx<float> *, cx<float> *, cx<float> *, cx<float> *, sc<float> *, cudaStream_t);
+template cudaError_t launch_tables_conn<double>(const double *, int, int, int, int, int, const int16_t *, const int16_t *, cx<double> *, cx<double> *, cx<double> *, cx<double> *, sc<double> *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_build_tables(const double *params, int N, int M, int K, cx<T> *Wt, cx<T> *b, cx<T> *a, cx<T> *logc,

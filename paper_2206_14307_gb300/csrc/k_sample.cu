@@ -202,36 +202,38 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
                 const int row = active ? row0 : 0;
                 const int r = row / md.G, g = row - r * md.G;
                 const int ku = md.perm[(size_t)g * N + iu], kd = md.perm[(size_t)g * N + id];
-                const size_t rs = (size_t)r * 2 * N * M;
-                // prefactor exponent: -2 (a_u - a_d) + 2 (CS_u - CS_d)
-                cx<T> C{T(0), T(0)};
-                {
-                    const cx<T> cu = md.CS[(size_t)r * N + ku], cd = md.CS[(size_t)r * N + kd];
-                    C = cx<T>{T(2) * (cu.x - cd.x), T(2) * (cu.y - cd.y)};
-                    if (md.use_bias) {
-                        const cx<T> au = md.avec[(size_t)r * N + ku], ad = md.avec[(size_t)r * N + kd];
-                        C.x -= T(2) * (au.x - ad.x);
-                        C.y -= T(2) * (au.y - ad.y);
-                    }
-                }
+                const size_t rs = (size_t)r * 2 * N * md.Mp;
+                const sc<T> *ESr = md.ES + (size_t)r * 2 * N;
                 for (int sg = 0; sg < md.nsign; ++sg) {
                     // site u holds +1: sigma = sign
                     const int t = row * md.nsign + sg;
-                    const cx<T> *Su = md.S4 + rs + ((size_t)sg * N + ku) * M;         // exp(-4 sigma W_u)
-                    const cx<T> *Sd = md.S4 + rs + ((size_t)(sg ^ 1) * N + kd) * M;   // exp(+4 sigma W_d)
-                    const cx<T> *pr_in = P0 + (size_t)t * M;
-                    cx<T> *pr_out = P1 + (size_t)t * M;
+                    const cx<T> *Su = md.S4 + rs + ((size_t)sg * N + ku) * md.Mp;         // exp(-4 sigma W_u)
+                    const cx<T> *Sd = md.S4 + rs + ((size_t)(sg ^ 1) * N + kd) * md.Mp;   // exp(+4 sigma W_d)
+                    const cx<T> *__restrict__ pr_in = P0 + (size_t)t * M;
+                    cx<T> *__restrict__ pr_out = P1 + (size_t)t * M;
+                    // loads of a block of JB hidden units first (the stores below do
+                    // not alias them), then the arithmetic and the stores
+                    constexpr int JB = MPL < 10 ? MPL : 8;
                     cx<T> prod{T(1), T(0)};
 #pragma unroll
-                    for (int j = 0; j < MPL; ++j) {
-                        const int m = gl + kSGL * j;
-                        if (m < M) {
-                            const cx<T> e2 = cmul(Su[m], Sd[m]);            // e^{2 Delta}
-                            const cx<T> tt{e2.x - T(1), e2.y};
-                            const cx<T> p = pr_in[m];
-                            const cx<T> f{T(1) + p.x * tt.x - p.y * tt.y, p.x * tt.y + p.y * tt.x};
-                            prod = cmul(prod, f);
-                            if (active) pr_out[m] = cdiv(cmul(p, e2), f);
+                    for (int j0 = 0; j0 < MPL; j0 += JB) {
+                        cx<T> pv_[JB], su_[JB], sd_[JB];
+#pragma unroll
+                        for (int jj = 0; jj < JB; ++jj) {
+                            const int m = gl + kSGL * (j0 + jj);
+                            if (j0 + jj < MPL && m < M) { pv_[jj] = pr_in[m]; su_[jj] = Su[m]; sd_[jj] = Sd[m]; }
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < JB; ++jj) {
+                            const int m = gl + kSGL * (j0 + jj);
+                            if (j0 + jj < MPL && m < M) {
+                                const cx<T> e2 = cmul(su_[jj], sd_[jj]);          // e^{2 Delta}
+                                const cx<T> tt{e2.x - T(1), e2.y};
+                                const cx<T> p = pv_[jj];
+                                const cx<T> f{T(1) + p.x * tt.x - p.y * tt.y, p.x * tt.y + p.y * tt.x};
+                                prod = cmul(prod, f);
+                                if (active) pr_out[m] = cdiv(cmul(p, e2), f);
+                            }
                         }
                     }
                     const int ex = expo<T>(prod.x, prod.y);
@@ -243,9 +245,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
                         pv = sc_mul(pv, w);
                     }
                     if (gl == 0 && active) {
-                        const T sgn = sg ? T(-1) : T(1);
+                        // prefactor exp(sigma (Cs_u - Cs_d)), sigma = sign
+                        const sc<T> pref = sc_mul(ESr[(size_t)sg * N + ku], ESr[(size_t)(sg ^ 1) * N + kd]);
                         const sc<T> term = T0[t];
-                        const sc<T> tn = sc_mul(sc_mul(term, pv), sc_exp(cx<T>{sgn * C.x, sgn * C.y}));
+                        const sc<T> tn = sc_mul(sc_mul(term, pv), pref);
                         T1[t] = tn;
                         so = sc_add(so, term);
                         sn = sc_add(sn, tn);
@@ -261,9 +264,17 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
             }
             if (lane == 0) { wold[warp] = so; wnew[warp] = sn; }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                sc<T> a = wold[0], b = wnew[0];
-                for (int w = 1; w < kSWarps; ++w) { a = sc_add(a, wold[w]); b = sc_add(b, wnew[w]); }
+            if (warp == 0) {
+                sc<T> a = lane < kSWarps ? wold[lane] : sc<T>{T(0), T(0), 0};
+                sc<T> b = lane < kSWarps ? wnew[lane] : sc<T>{T(0), T(0), 0};
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const sc<T> x{shfl_x(a.x, o), shfl_x(a.y, o), __shfl_xor_sync(0xffffffffu, a.e, o)};
+                    const sc<T> y{shfl_x(b.x, o), shfl_x(b.y, o), __shfl_xor_sync(0xffffffffu, b.e, o)};
+                    a = sc_add(a, x);
+                    b = sc_add(b, y);
+                }
+                if (lane == 0) {
                 const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
                 const double r2 = (bx * bx + by * by) / (ax * ax + ay * ay) * ldexp(1.0, 2 * (b.e - a.e));
                 const int acc_now = (double)u_sh < r2;
@@ -276,6 +287,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
                     if (step >= n_burn) ++n_acc;
                 }
                 accept = acc_now;
+                }
             }
             __syncthreads();
             // ---- keep every n_skip-th state after burn-in ----

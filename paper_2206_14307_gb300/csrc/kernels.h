@@ -55,6 +55,7 @@ cudaError_t launch_build_tables(const double *params, int N, int M, int K, cx<T>
 
 template <typename T>
 cudaError_t launch_tables_conn(const double *params, int N, int M, int K, int nb, int use_bias, const int16_t *bi,
-                               const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, cudaStream_t st);
+                               const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, sc<T> *ES,
+                               cudaStream_t st);
 
 }  // namespace nnqs
