@@ -134,10 +134,13 @@ int nnqs_sample(nnqs_model *model, uint64_t seed, int32_t n_chains, int32_t n_pe
                 int32_t n_skip, int32_t n_burn, uint64_t *cfg_out, float *acc_out, void *stream);
 
 /* log psi(s) for n configurations (Eqs. 2-6): logpsi_out [n][2] doubles
- * (re, im), Im in (-pi, pi].  cfg: [n][ceil(N/64)].  With NNQS_BF16X2/X3 the
- * theta products of all n*K*|G| transformed configurations run as one
- * tcgen05 GEMM.  A configuration whose amplitude vanishes by symmetry
- * returns re = -inf. */
+ * (re, im), Im in (-pi, pi].  cfg: [n][ceil(N/64)].  With NNQS_BF16X2/X3 and
+ * M <= 128 the theta products of all n*K*|G| transformed configurations run
+ * on the tcgen05 tensor cores (bf16 split weights, fp32 accumulation in
+ * TMEM) with the log-cosh and projection sums fused into the epilogue; other
+ * sizes use the FP32 form.  Accuracy of theta: 2^-17 (two terms) or 2^-25
+ * (three terms) relative to sum_j |W_mj|.  A configuration whose amplitude
+ * vanishes by symmetry returns re = -inf. */
 int nnqs_log_psi(nnqs_model *model, const uint64_t *cfg, int64_t n, double *logpsi_out, void *stream);
 
 /* Local energy (Sec. 3.2, Eq. 10): E_loc(s) = sum_s' H_{s s'} psi(s')/psi(s)

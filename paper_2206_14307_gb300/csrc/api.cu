@@ -121,6 +121,10 @@ struct nnqs_model {
     void *Wt = nullptr, *b = nullptr, *a = nullptr, *logc = nullptr, *X = nullptr, *XA = nullptr;
     void *Tb = nullptr, *Cb = nullptr, *S4 = nullptr, *CS = nullptr, *ES = nullptr;
     uint16_t *bperm = nullptr;
+    // tensor-core path (NNQS_BF16X2 / NNQS_BF16X3)
+    int ns = 0;                  // bf16 terms of the split (0: tensor-core path off)
+    uint16_t *bimg = nullptr;    // shared-memory images of the split weights
+    uint8_t *pinv = nullptr;     // inverse permutations [G][N]
     int *status = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -250,8 +254,22 @@ int nnqs_create(const nnqs_desc *desc, nnqs_model **out)
     ALLOC(m->ES, K * 2 * N * (m->fp64 ? sizeof(sc<double>) : sizeof(sc<float>)));
     ALLOC(m->bperm, (size_t)m->G * bi.size() * sizeof(uint16_t));
     ALLOC(m->status, sizeof(int));
+    if (d.precision == NNQS_BF16X2 || d.precision == NNQS_BF16X3) {
+        const int ns = d.precision == NNQS_BF16X2 ? 2 : 3;
+        if (tc_supported((int)N, d.M, m->G, d.K, m->nsign, ns)) {
+            m->ns = ns;
+            ALLOC(m->bimg, tc_bimg_bytes((int)N, d.M, d.K, ns));
+            ALLOC(m->pinv, (size_t)m->G * N);
+        }
+    }
 #undef ALLOC
     cudaMemcpy(m->perm, perm.data(), perm.size(), cudaMemcpyHostToDevice);
+    if (m->pinv) {
+        std::vector<uint8_t> inv(perm.size());
+        for (int g = 0; g < m->G; ++g)
+            for (int i = 0; i < m->N; ++i) inv[(size_t)g * m->N + perm[(size_t)g * m->N + i]] = (uint8_t)i;
+        cudaMemcpy(m->pinv, inv.data(), inv.size(), cudaMemcpyHostToDevice);
+    }
     {
         // image of every bond under every group element, with the orientation flag
         std::vector<int> index((size_t)N * N, -1);
@@ -292,7 +310,7 @@ int nnqs_destroy(nnqs_model *m)
     if (!m) return NNQS_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {m->perm, m->bi, m->bj, m->bt, m->chi, m->params, m->Wt, m->b, m->a, m->logc, m->X, m->XA,
-                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->ws};
+                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->ws, m->bimg, m->pinv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -330,6 +348,10 @@ int nnqs_set_params_device(nnqs_model *m, const double *params, int64_t P, void 
                                           (cx<float> *)m->Tb, (cx<float> *)m->Cb, (cx<float> *)m->S4,
                                           (cx<float> *)m->CS, (sc<float> *)m->ES, st);
         if (e != cudaSuccess) return cuda_fail(e, "build connection tables");
+        if (m->ns) {
+            e = launch_bimg(m->params, m->N, m->d.M, m->d.K, m->ns, m->bimg, st);
+            if (e != cudaSuccess) return cuda_fail(e, "build bf16 weight images");
+        }
         return NNQS_OK;
     });
 }
@@ -355,8 +377,10 @@ int nnqs_log_psi(nnqs_model *m, const uint64_t *cfg, int64_t n, double *out, voi
     if (!cfg || !out) return fail(NNQS_EINVAL, "cfg and logpsi_out must be non-NULL");
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
-        cudaError_t e = m->fp64 ? launch_log_psi(view<double>(m), cfg, n, out, m->nsm, st)
-                                : launch_log_psi(view<float>(m), cfg, n, out, m->nsm, st);
+        cudaError_t e;
+        if (m->fp64) e = launch_log_psi(view<double>(m), cfg, n, out, m->nsm, st);
+        else if (m->ns) e = launch_log_psi_tc(view<float>(m), m->bimg, m->pinv, m->ns, cfg, n, out, m->nsm, st);
+        else e = launch_log_psi(view<float>(m), cfg, n, out, m->nsm, st);
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "log_psi");
     });
 }

@@ -165,6 +165,23 @@ __device__ __forceinline__ void cosh2(cx<T> th, cx<T> &mant, int &k, cx<T> &p)
     p = neg ? cx<T>{T(1) - pp.x, -pp.y} : pp;
 }
 
+// 2 cosh(theta) = mant * 2^k only (no p)
+template <typename T> __device__ __forceinline__ void cosh2_mant(cx<T> th, cx<T> &mant, int &k)
+{
+    const T l2e = T(1.4426950408889634);
+    const bool neg = th.x < T(0);
+    const T u = fabs(th.x);
+    const T v = neg ? -th.y : th.y;
+    const T t = u * l2e;
+    const T kf = floor(t);
+    const T ef = exp2(t - kf);
+    const T q = exp2(T(-2) * t);
+    T sv, cv;
+    sincos(v, &sv, &cv);
+    mant = cx<T>{ef * cv * (T(1) + q), ef * sv * (T(1) - q)};
+    k = (int)kf;
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
 struct u32x4 { uint32_t v[4]; };
 __device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1)

@@ -78,7 +78,8 @@ __device__ __forceinline__ sc<T> row_cosh(const DevModel<T> &md, int r, int sign
             if (md.use_bias) { cx<T> b = br[m]; th.x += b.x; th.y += b.y; }
             cx<T> mant;
             int k;
-            cosh2(th, mant, k, p[j]);
+            cosh2_mant(th, mant, k);
+            p[j] = cx<T>{T(0), T(0)};
             cx<T> q = cmul(mk(prod.x, prod.y), mant);
             prod = sc<T>{q.x, q.y, prod.e + k};
         } else {

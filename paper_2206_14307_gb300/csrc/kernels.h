@@ -58,4 +58,11 @@ cudaError_t launch_tables_conn(const double *params, int N, int M, int K, int nb
                                const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, sc<T> *ES,
                                cudaStream_t st);
 
+// tensor-core (tcgen05) log psi with BF16-split weights: NS = 2 or 3 terms
+bool tc_supported(int N, int M, int G, int K, int nsign, int NS);
+size_t tc_bimg_bytes(int N, int M, int K, int NS);
+cudaError_t launch_bimg(const double *params, int N, int M, int K, int NS, uint16_t *img, cudaStream_t st);
+cudaError_t launch_log_psi_tc(const DevModel<float> &md, const uint16_t *bimg, const uint8_t *pinv, int NS,
+                              const uint64_t *cfg, int64_t n, double *out, int nsm, cudaStream_t st);
+
 }  // namespace nnqs

@@ -1,0 +1,59 @@
+"""log psi with the theta GEMM on the tcgen05 tensor cores (BF16-split
+weights) against the FP64 oracle and against the FP32 SIMT form.
+
+Tolerance: |log psi| absolute <= 1e-5 (Im modulo 2 pi).  The split's error on
+theta is <= 2^-17 sum_j |W_mj| (two terms) or 2^-25 (three terms), and the
+tensor core's FP32 accumulator adds rounding at the scale of the partial sums
+of the NS*N products (|partial| up to sum_j |W_mj|).  At the workloads' weight
+scale (std 0.01) both splits meet 1e-5; at the 0.05 stress scale the
+three-term split meets it up to 6x6, while for 8x8 with M = 128 (192 products
+per theta, sum |W| ~ 2.6) the accumulator limits it to 1e-4.
+"""
+import numpy as np
+import pytest
+
+from paper_2206_14307_gb300 import synth
+from tests.helpers import annihilated, assert_logpsi_close, make_pair, to_complex
+
+pytestmark = pytest.mark.gpu
+BF16X2, BF16X3, FP32 = 2, 3, 1
+
+CASES = [
+    # L, K, M, proj, inv, bias, momentum, irrep, n, (precision, std) pairs
+    # (|G| = 1, 128, 288, 512 -> samples per super-tile S = 128, 1, 4, 1)
+    (4, 1, 16, False, 0, True, 0, 0, 300, [(BF16X2, 0.01), (BF16X3, 0.01), (BF16X3, 0.05)]),
+    # a B1 irrep at (pi, pi) nearly cancels for weights ~0.01 (Sum|terms| >> |psi|,
+    # which FP32 cannot resolve to 1e-5): tested at 0.2 with the three-term split
+    (4, 2, 12, True, 1, True, 1, 2, 37, [(BF16X3, 0.2)]),
+    (6, 1, 72, True, 1, True, 0, 0, 45, [(BF16X2, 0.01), (BF16X3, 0.01), (BF16X3, 0.05)]),
+    (6, 1, 72, True, 0, False, 0, 0, 9, [(BF16X2, 0.01), (BF16X3, 0.05)]),
+    (8, 1, 128, True, 0, True, 0, 0, 5, [(BF16X2, 0.01), (BF16X3, 0.05)]),
+]
+TOL_STRESS_LARGE = 1e-4   # 8x8, M = 128 at std 0.05 (accumulator rounding, see above)
+PARAMS = [(c[:9], ps) for c in CASES for ps in c[9]]
+
+
+@pytest.mark.parametrize("case,ps", PARAMS)
+def test_log_psi_tensor_core_vs_oracle(case, ps):
+    L, K, M, proj, inv, bias, mom, irr, n = case
+    prec, std = ps
+    om, gm, _ = make_pair(L, K=K, M=M, proj=proj, spin_inv=inv, use_bias=bias, momentum=mom, irrep=irr,
+                          std=std, precision=prec, logc_std=0.2 if K > 1 else None)
+    s = synth.random_sz0(L * L, 3 * n, seed=11)
+    s = s[~annihilated(L, s, proj, mom, irr, inv, bias)][:n]
+    from paper_2206_14307_gb300 import nnqs
+    got = to_complex(gm.log_psi(nnqs.cfg_tensor(synth.pack(s))))
+    gm.status()
+    want = om.log_psi(s)
+    assert_logpsi_close(got, want, TOL_STRESS_LARGE if (M >= 128 and std > 0.01) else 1e-5)
+
+
+def test_tensor_core_matches_fp32_form_on_many_samples():
+    # 6x6 workload shape, 1001 samples (ragged against S = 4), both forms on the GPU
+    _, g16, p = make_pair(6, K=1, M=72, proj=True, spin_inv=1, std=0.01, precision=BF16X2)
+    _, g32, _ = make_pair(6, K=1, M=72, proj=True, spin_inv=1, std=0.01, precision=FP32)
+    s = synth.random_sz0(36, 1001, seed=12)
+    from paper_2206_14307_gb300 import nnqs
+    c = nnqs.cfg_tensor(synth.pack(s))
+    assert_logpsi_close(to_complex(g16.log_psi(c)), to_complex(g32.log_psi(c)), 1e-5)
+    g16.status()
