@@ -9,12 +9,15 @@ K = (0,0); parameters N(0, 0.01^2) per real and imaginary part (seed 2206).
 One step = one pass of the hot path:
   nnqs_sample         1024 chains x 16 kept samples, n_skip = 10, n_burn = 100
                       (266,240 Metropolis proposals, each a full psi(s')/psi(s))
+  nnqs_log_psi        fresh log psi of the 16,384 samples: the theta GEMM of
+                      16,384 x 288 transformed configurations on the tcgen05
+                      tensor cores (bf16 hi + lo split weights, fp32 accumulate)
   nnqs_local_energy   E_loc of the 16,384 samples (every anti-aligned J1/J2 bond
                       -> one connected amplitude) with the FP64 sums of E_loc.
 Metric: projected-RBM amplitude evaluations per second (one evaluation = one
-psi(s') over all K|G| x 2 x M hidden terms: sampler proposals + connected
-configurations of E_loc + one fresh amplitude per sample), and E_loc
-samples/s; the same step in the plain FP64 GPU form is timed beside it.
+psi(s') over all K|G| x 2 x M hidden terms: sampler proposals + fresh
+amplitudes + connected configurations of E_loc), and E_loc samples/s; the same
+step in the plain FP64 GPU form is timed beside it.
 
 Timing: CUDA events on the launching stream, per step, with a 512 MB L2 flush
 before every timed step (outside the events); W warm-up steps; barrier and the
@@ -44,9 +47,10 @@ N_SAMPLES = N_CHAINS * N_PER_CHAIN
 PARAM_STD, PARAM_SEED = 0.01, 2206
 WORKLOAD = "6x6 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=72), 288 ops + spin inversion; 1024 chains x 16 samples"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
+BF16_PEAK_TFLOPS = 1900.3   # measured dense bf16 burst figure of the GB300s
 FLOPS_PER_ELEMENT = 28   # one connected factor p e^D + (1-p) e^-D and its running product
 # DRAM bytes (read + write) per E_loc launch of this workload: the ncu capture of
-# profiles/k_eloc_k_sample_6x6_small.md measured 0.42 MB for 2048 samples; the
+# profiles/vmc_step_6x6.md measured 0.42 MB for 2048 samples; the
 # traffic grows with the samples, so a 16384-sample launch moves 8x that.
 K_RATIO_TRAFFIC = 8 * 0.418304e6
 
@@ -128,6 +132,7 @@ def gpu_arm(args, rank, world):
         return m
 
     cfg = torch.empty(N_SAMPLES, 1, dtype=torch.int64, device="cuda")
+    logpsi = torch.empty(N_SAMPLES, 2, dtype=torch.float64, device="cuda")
     acc = torch.empty(N_CHAINS, dtype=torch.float32, device="cuda")
     eloc = torch.empty(N_SAMPLES, 2, dtype=torch.float64, device="cuda")
     sums = torch.empty(4, dtype=torch.float64, device="cuda")
@@ -142,6 +147,7 @@ def gpu_arm(args, rank, world):
             params_dev.copy_(params_pinned, non_blocking=True)
             model.set_params(params_dev.view(-1, 2))
         model.sample(seed, N_CHAINS, N_PER_CHAIN, N_SKIP, N_BURN, cfg_out=cfg, acc_out=acc)
+        model.log_psi(cfg, out=logpsi)
         model.local_energy(cfg, out=eloc, sums=sums)
         if e2e:
             sums_host.copy_(sums, non_blocking=True)
@@ -152,49 +158,52 @@ def gpu_arm(args, rank, world):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        tot, tk = 0.0, 0.0
+        tot, tk, tl = 0.0, 0.0, 0.0
         for k in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(st)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            ev[0].record(st)
             seed = 14307 + 1000003 * rank + warmup + k
             if e2e:
                 params_dev.copy_(params_pinned, non_blocking=True)
                 model.set_params(params_dev.view(-1, 2))
             model.sample(seed, N_CHAINS, N_PER_CHAIN, N_SKIP, N_BURN, cfg_out=cfg, acc_out=acc)
-            ka.record(st)
+            ev[1].record(st)
+            model.log_psi(cfg, out=logpsi)
+            ev[2].record(st)
             model.local_energy(cfg, out=eloc, sums=sums)
-            kb.record(st)
+            ev[3].record(st)
             if e2e:
                 sums_host.copy_(sums, non_blocking=True)
-            b.record(st)
-            b.synchronize()
-            tot += a.elapsed_time(b)
-            tk += ka.elapsed_time(kb)
+            ev[4].record(st)
+            ev[4].synchronize()
+            tot += ev[0].elapsed_time(ev[4])
+            tl += ev[1].elapsed_time(ev[2])
+            tk += ev[2].elapsed_time(ev[3])
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        return tot / steps, tk / steps
+        return tot / steps, tk / steps, tl / steps
 
-    m32 = make(nnqs.FP32)
+    m32 = make(nnqs.BF16X2)
     with ClockSampler(dev) as clk:
-        ms, ms_eloc = timed(m32, args.steps, args.warmup)
+        ms, ms_eloc, ms_logpsi = timed(m32, args.steps, args.warmup)
     m32.status()
-    e2e_ms, _ = timed(m32, args.steps, max(1, args.warmup // 2), e2e=True)
+    e2e_ms, _, _ = timed(m32, args.steps, max(1, args.warmup // 2), e2e=True)
     words = cfg.cpu().numpy().view(np.uint64)
     nb = n_antialigned(words)
     proposals = N_CHAINS * (N_BURN + N_PER_CHAIN * N_SKIP)
     evals = proposals + nb + N_SAMPLES
     G, nsign = m32.G, 2
     elements = nb * G * nsign * M
-    res = dict(ms=ms, ms_eloc=ms_eloc, e2e_ms=e2e_ms, evals=evals, nb=nb, elements=elements,
-               clocks=clk.summary(), acc=float(acc.mean().item()), e_mean=float(eloc[:, 0].mean().item()) / N)
+    res = dict(ms=ms, ms_eloc=ms_eloc, ms_logpsi=ms_logpsi, e2e_ms=e2e_ms, evals=evals, nb=nb, elements=elements,
+               clocks=clk.summary(), acc=float(acc.mean().item()), e_mean=float(eloc[:, 0].mean().item()) / N,
+               G=G)
     if not args.no_fp64:
         m64 = make(nnqs.FP64)
-        ms64, ms64_eloc = timed(m64, args.fp64_steps, 1)
-        res.update(ms64=ms64, ms64_eloc=ms64_eloc)
+        ms64, ms64_eloc, ms64_logpsi = timed(m64, args.fp64_steps, 1)
+        res.update(ms64=ms64, ms64_eloc=ms64_eloc, ms64_logpsi=ms64_logpsi)
         m64.close()
     m32.close()
     return res
@@ -298,14 +307,17 @@ def main():
         return
     value = world * res["evals"] / (ms / 1e3)
     eloc_ach = res["elements"] * FLOPS_PER_ELEMENT / (res["ms_eloc"] / 1e3) / 1e12
+    # theta GEMM: algorithmic 4 K|G| M N flop per fresh amplitude (complex W times +-1 configurations)
+    gemm_flop = 4.0 * res["G"] * M * N * N_SAMPLES
+    gemm_ach = gemm_flop / (res["ms_logpsi"] / 1e3) / 1e12
     line = {
-        "metric": "projected-RBM amplitude evals/s (E_loc samples/s beside); FP32 form vs plain FP64 GPU form",
+        "metric": "projected-RBM amplitude evals/s (E_loc samples/s beside); BF16-split/FP32 form vs plain FP64 GPU form",
         "value": value, "unit": "amplitude evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2+f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "L": L, "M": M, "G": 288, "spin_inversion": True,
                    "chains": N_CHAINS, "samples_per_chain": N_PER_CHAIN, "n_skip": N_SKIP, "n_burn": N_BURN,
-                   "precision": "FP32 (exact exponent tracking)", "l2": "flushed (512 MB write) before every step"},
+                   "precision": "BF16X2 theta GEMM on tensor cores for fresh amplitudes; FP32 with exact exponent tracking elsewhere", "l2": "flushed (512 MB write) before every step"},
         "eloc_samples_per_s": world * N_SAMPLES / (ms / 1e3),
         "acceptance": res["acc"], "E_loc_mean_per_site": res["e_mean"],
         "roofline": {"kernel": "k_eloc (E_loc connected-amplitude engine)", "bound": "alu",
@@ -313,14 +325,21 @@ def main():
                      "frac": eloc_ach / FP32_PEAK_TFLOPS, "traffic": K_RATIO_TRAFFIC,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",
                      "work": f"{res['elements']} connected elements x {FLOPS_PER_ELEMENT} flop"},
+        "theta_gemm": {"kernel": "k_logpsi_tc (tcgen05 theta GEMM + fused log-cosh epilogue)", "bound": "tensor",
+                       "achieved": gemm_ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": gemm_ach / BF16_PEAK_TFLOPS, "peak_source": "MEASURED bf16 burst (of measured)",
+                       "fresh_amplitudes_per_s": N_SAMPLES / (res["ms_logpsi"] / 1e3),
+                       "note": "algorithmic flop (4 K|G| M N per amplitude); the bf16 hi+lo split executes 2x; "
+                               "the kernel is limited by its log-cosh epilogue, not the MMA"},
         "e2e": {"value": world * res["evals"] / (e2e_ms / 1e3), "unit": "amplitude evals/s",
                 "h2d_bytes_per_step": 2665 * 16, "d2h_bytes_per_step": 32},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 5 * args.steps,
         "clocks": res["clocks"],
     }
     if "ms64" in res:
         line["fp64_gpu"] = {"value": world * res["evals"] / (res["ms64"] / 1e3), "unit": "amplitude evals/s",
-                            "ms_per_step": res["ms64"], "steps": args.fp64_steps, "warmup": 1}
+                            "ms_per_step": res["ms64"], "steps": args.fp64_steps, "warmup": 1,
+                            "fresh_amplitudes_per_s": N_SAMPLES / (res["ms64_logpsi"] / 1e3)}
         line["speedup_vs_fp64_gpu"] = res["ms64"] / ms
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
