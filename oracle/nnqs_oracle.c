@@ -291,13 +291,39 @@ static cplx eloc_one(const or_model *h, const int8_t *s, cplx lp)
 
 void or_local_energy(void *hp, const int8_t *spins, int n, double *eloc)
 {
+    /* Same sums as eloc_one, with every (sample, bond) ratio evaluated in
+     * parallel and then added in bond order. */
     const or_model *h = (const or_model *)hp;
+    const int nb = h->nb;
+    cplx *lp = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    cplx *ratio = (cplx *)calloc((size_t)n * nb, sizeof(cplx));
     #pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < n; ++k) lp[k] = log_psi_one(h, spins + (size_t)k * h->N);
+    #pragma omp parallel for schedule(dynamic)
+    for (long q = 0; q < (long)n * nb; ++q) {
+        const int k = (int)(q / nb), b = (int)(q % nb);
+        const int8_t *s = spins + (size_t)k * h->N;
+        const int i = h->bi[b], j = h->bj[b];
+        if (s[i] == s[j]) continue;
+        int8_t *sp = (int8_t *)malloc(h->N);
+        memcpy(sp, s, h->N);
+        sp[i] = s[j]; sp[j] = s[i];
+        ratio[q] = cexp(log_psi_one(h, sp) - lp[k]);
+        free(sp);
+    }
     for (int k = 0; k < n; ++k) {
         const int8_t *s = spins + (size_t)k * h->N;
-        cplx e = eloc_one(h, s, log_psi_one(h, s));
+        cplx off = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int i = h->bi[b], j = h->bj[b];
+            if (s[i] == s[j]) continue;
+            const double J = h->bt[b] == 1 ? h->J1 : h->J2;
+            off += 0.5 * J * ratio[(size_t)k * nb + b];
+        }
+        const cplx e = diag_energy(h, s) + off;
         eloc[2 * k] = creal(e); eloc[2 * k + 1] = cimag(e);
     }
+    free(lp); free(ratio);
 }
 
 /* Lanczos-step quantities (Sec. 3.3): h1 = (H psi)(s)/psi(s) and
