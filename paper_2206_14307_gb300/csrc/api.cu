@@ -488,31 +488,52 @@ int nnqs_grad_logpsi(nnqs_model *m, const uint64_t *cfg, int64_t n, double *O, v
     });
 }
 
-int nnqs_energy_grad(const nnqs_model *mc, const double *O, const double *eloc, int64_t n, double *F, void *stream)
+int nnqs_energy_grad(const nnqs_model *mc, const double *O, const double *eloc, const double *weights, int64_t n,
+                     double *F, void *stream)
 {
     nnqs_model *m = const_cast<nnqs_model *>(mc);
     if (check_model(m)) return NNQS_EINVAL;
     if (n <= 0) return fail(NNQS_EINVAL, "n must be > 0");
     if (!O || !eloc || !F) return fail(NNQS_EINVAL, "O, eloc and F_out must be non-NULL");
     return with_device(m, [&]() -> int {
-        int rc = ensure_ws(m, 256);
+        int rc = ensure_ws(m, 256 * sizeof(double));
         if (rc) return rc;
-        cudaError_t e = launch_energy_grad(O, eloc, n, m->P, F, (double *)m->ws, (cudaStream_t)stream);
+        cudaError_t e = launch_energy_grad(O, eloc, weights, n, m->P, F, (double *)m->ws, (cudaStream_t)stream);
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "energy_grad");
     });
 }
 
-int nnqs_sr_matvec(const nnqs_model *mc, const double *O, int64_t n, const double *x, double lambda, double *y, void *stream)
+int nnqs_sr_matvec(const nnqs_model *mc, const double *O, const double *weights, int64_t n, const double *x,
+                   double lambda, double *y, void *stream)
 {
     nnqs_model *m = const_cast<nnqs_model *>(mc);
     if (check_model(m)) return NNQS_EINVAL;
     if (n <= 0) return fail(NNQS_EINVAL, "n must be > 0");
     if (!O || !x || !y) return fail(NNQS_EINVAL, "O, x and y must be non-NULL");
     return with_device(m, [&]() -> int {
-        int rc = ensure_ws(m, align256((size_t)(2 * n + 2) * sizeof(double)));
+        int rc = ensure_ws(m, sr_scratch_doubles(n, m->P) * sizeof(double));
         if (rc) return rc;
-        cudaError_t e = launch_sr_matvec(O, n, m->P, x, lambda, y, (double *)m->ws, (cudaStream_t)stream);
+        cudaError_t e = launch_sr_matvec(O, weights, n, m->P, x, lambda, y, (double *)m->ws, (cudaStream_t)stream);
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "sr_matvec");
+    });
+}
+
+int nnqs_sr_solve(const nnqs_model *mc, const double *O, const double *weights, int64_t n, const double *F,
+                  double lambda, double dtau, int32_t max_iter, double tol, double *delta, double *info,
+                  double *params_inout, void *stream)
+{
+    nnqs_model *m = const_cast<nnqs_model *>(mc);
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n <= 0) return fail(NNQS_EINVAL, "n must be > 0");
+    if (max_iter < 0 || max_iter > 100000) return fail(NNQS_EINVAL, "max_iter must be in 0..100000");
+    if (!(lambda >= 0) || !(tol >= 0)) return fail(NNQS_EINVAL, "lambda and tol must be >= 0");
+    if (!O || !F || !delta) return fail(NNQS_EINVAL, "O, F and delta_out must be non-NULL");
+    return with_device(m, [&]() -> int {
+        int rc = ensure_ws(m, sr_scratch_doubles(n, m->P) * sizeof(double));
+        if (rc) return rc;
+        cudaError_t e = launch_sr_solve(O, weights, n, m->P, F, lambda, dtau, max_iter, tol, delta, info,
+                                        params_inout, (double *)m->ws, (cudaStream_t)stream);
+        return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "sr_solve");
     });
 }
 

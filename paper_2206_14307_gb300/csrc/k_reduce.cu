@@ -105,93 +105,6 @@ cudaError_t launch_eloc_sums(const double *eloc, int64_t n, double *partial, int
     return cudaGetLastError();
 }
 
-// mean of a complex vector (one block, fixed order)
-__global__ void __launch_bounds__(kRedThreads) k_cmean(const double *__restrict__ v, int64_t n, double *__restrict__ out)
-{
-    __shared__ double sh[kRedThreads / 32][2];
-    double a[2] = {0, 0};
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) { a[0] += v[2 * k]; a[1] += v[2 * k + 1]; }
-    block_sum<2>(a, sh);
-    if (threadIdx.x == 0) { out[0] = a[0] / (double)n; out[1] = a[1] / (double)n; }
-}
-
-// F_k = (1/n) sum_s conj(O_sk) (e_s - ebar)
-__global__ void k_energy_grad(const double *__restrict__ O, const double *__restrict__ e, const double *__restrict__ ebar,
-                              int64_t n, int64_t P, double *__restrict__ F)
-{
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= P) return;
-    const double bx = ebar[0], by = ebar[1];
-    double fx = 0, fy = 0;
-    for (int64_t s = 0; s < n; ++s) {
-        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
-        const double dx = e[2 * s] - bx, dy = e[2 * s + 1] - by;
-        fx += ox * dx + oy * dy;
-        fy += ox * dy - oy * dx;
-    }
-    F[2 * k] = fx / (double)n;
-    F[2 * k + 1] = fy / (double)n;
-}
-
-cudaError_t launch_energy_grad(const double *O, const double *eloc, int64_t n, int64_t P, double *F, double *scratch,
-                               cudaStream_t st)
-{
-    k_cmean<<<1, kRedThreads, 0, st>>>(eloc, n, scratch);
-    const int tb = 256;
-    k_energy_grad<<<(unsigned)((P + tb - 1) / tb), tb, 0, st>>>(O, eloc, scratch, n, P, F);
-    return cudaGetLastError();
-}
-
-// z_s = sum_k O_sk x_k  (one block per sample)
-__global__ void __launch_bounds__(kRedThreads) k_ov(const double *__restrict__ O, const double *__restrict__ x, int64_t P,
-                                                    double *__restrict__ z)
-{
-    __shared__ double sh[kRedThreads / 32][2];
-    const int64_t s = blockIdx.x;
-    double a[2] = {0, 0};
-    for (int64_t k = threadIdx.x; k < P; k += blockDim.x) {
-        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
-        const double xx = x[2 * k], xy = x[2 * k + 1];
-        a[0] += ox * xx - oy * xy;
-        a[1] += ox * xy + oy * xx;
-    }
-    block_sum<2>(a, sh);
-    if (threadIdx.x == 0) { z[2 * s] = a[0]; z[2 * s + 1] = a[1]; }
-}
-
-// y_k = (1/n) sum_s conj(O_sk) z_s - conj(Obar_k) zbar + lambda x_k
-__global__ void k_sr_out(const double *__restrict__ O, const double *__restrict__ z, const double *__restrict__ zbar,
-                         const double *__restrict__ x, double lambda, int64_t n, int64_t P, double *__restrict__ y)
-{
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= P) return;
-    double ax = 0, ay = 0, mx = 0, my = 0;
-    for (int64_t s = 0; s < n; ++s) {
-        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
-        const double zx = z[2 * s], zy = z[2 * s + 1];
-        ax += ox * zx + oy * zy;
-        ay += ox * zy - oy * zx;
-        mx += ox; my += oy;
-    }
-    const double inv = 1.0 / (double)n;
-    ax *= inv; ay *= inv; mx *= inv; my *= inv;
-    const double bx = zbar[0], by = zbar[1];
-    y[2 * k] = ax - (mx * bx + my * by) + lambda * x[2 * k];
-    y[2 * k + 1] = ay - (mx * by - my * bx) + lambda * x[2 * k + 1];
-}
-
-cudaError_t launch_sr_matvec(const double *O, int64_t n, int64_t P, const double *x, double lambda, double *y,
-                             double *scratch, cudaStream_t st)
-{
-    double *z = scratch;            // [n][2]
-    double *zbar = scratch + 2 * n; // [2]
-    k_ov<<<(unsigned)n, kRedThreads, 0, st>>>(O, x, P, z);
-    k_cmean<<<1, kRedThreads, 0, st>>>(z, n, zbar);
-    const int tb = 256;
-    k_sr_out<<<(unsigned)((P + tb - 1) / tb), tb, 0, st>>>(O, z, zbar, x, lambda, n, P, y);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------
 // parameter-derived tables (computed in FP64, stored in T)
 // ---------------------------------------------------------------------------

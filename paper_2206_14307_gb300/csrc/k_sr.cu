@@ -1,0 +1,259 @@
+// k_sr.cu -- stochastic reconfiguration pieces (Eq. 12), FP64 throughout.
+//
+//   F_k   = <conj(O_k) (E_loc - <E_loc>)>
+//   S x   = <conj(O) (O x)> - <conj(O)> <O x>,    (S + lambda I) x
+//   solve (S + lambda I) delta = -dtau F by conjugate gradients (Hermitian
+//   positive definite for lambda > 0), matrix-free, with the CG scalars kept
+//   in device memory so that a solve needs no host synchronisation; after
+//   convergence (|r| <= tol |b|) the remaining iterations do nothing.
+// Means are over samples with optional weights w_s (NULL: all 1).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nnqs {
+
+constexpr int kSrThreads = 256;
+constexpr int kDotBlocks = 128;
+
+// scratch layout (doubles)
+//   [0, 16)          CG state: 0 rr, 1 pAp, 2 alpha, 3 beta, 4 |b|^2, 5 done, 6 iterations, 7 W, 8-9 mean
+//   [16, 16+2*kDot)  partial sums
+//   then z [n][2], r [P][2], p [P][2], Ap [P][2]
+enum { S_RR = 0, S_PAP = 1, S_ALPHA = 2, S_BETA = 3, S_B2 = 4, S_DONE = 5, S_IT = 6, S_W = 7, S_MEAN = 8 };
+constexpr int kStateDoubles = 16;
+
+size_t sr_scratch_doubles(int64_t n, int64_t P)
+{
+    return kStateDoubles + 2 * kDotBlocks + 2 * (size_t)n + 6 * (size_t)P + 64;
+}
+
+template <int NV>
+__device__ __forceinline__ void blk_sum(double (&v)[NV], double (*sh)[NV])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) sh[0][q] += sh[w][q];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = sh[0][q];
+    }
+}
+
+// weighted mean of a complex vector and the weight total (one block, fixed order)
+__global__ void __launch_bounds__(kSrThreads) k_wmean(const double *__restrict__ v, const double *__restrict__ w,
+                                                      int64_t n, double *__restrict__ state)
+{
+    __shared__ double sh[kSrThreads / 32][3];
+    double a[3] = {0, 0, 0};
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const double wk = w ? w[k] : 1.0;
+        a[0] += wk * v[2 * k];
+        a[1] += wk * v[2 * k + 1];
+        a[2] += wk;
+    }
+    blk_sum<3>(a, sh);
+    if (threadIdx.x == 0) {
+        state[S_MEAN] = a[0] / a[2];
+        state[S_MEAN + 1] = a[1] / a[2];
+        state[S_W] = a[2];
+    }
+}
+
+// F_k = (1/W) sum_s w_s conj(O_sk) (e_s - ebar)
+__global__ void k_energy_grad(const double *__restrict__ O, const double *__restrict__ e, const double *__restrict__ w,
+                              const double *__restrict__ state, int64_t n, int64_t P, double *__restrict__ F)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const double bx = state[S_MEAN], by = state[S_MEAN + 1], W = state[S_W];
+    double fx = 0, fy = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const double ws = w ? w[s] : 1.0;
+        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
+        const double dx = e[2 * s] - bx, dy = e[2 * s + 1] - by;
+        fx += ws * (ox * dx + oy * dy);
+        fy += ws * (ox * dy - oy * dx);
+    }
+    F[2 * k] = fx / W;
+    F[2 * k + 1] = fy / W;
+}
+
+cudaError_t launch_energy_grad(const double *O, const double *eloc, const double *w, int64_t n, int64_t P, double *F,
+                               double *scratch, cudaStream_t st)
+{
+    k_wmean<<<1, kSrThreads, 0, st>>>(eloc, w, n, scratch);
+    k_energy_grad<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(O, eloc, w, scratch, n, P, F);
+    return cudaGetLastError();
+}
+
+// z_s = sum_k O_sk x_k  (one block per sample); skipped once the solve converged
+__global__ void __launch_bounds__(kSrThreads) k_ov(const double *__restrict__ O, const double *__restrict__ x, int64_t P,
+                                                   double *__restrict__ z, const double *__restrict__ state)
+{
+    if (state && state[S_DONE] != 0.0) return;
+    __shared__ double sh[kSrThreads / 32][2];
+    const int64_t s = blockIdx.x;
+    double a[2] = {0, 0};
+    for (int64_t k = threadIdx.x; k < P; k += blockDim.x) {
+        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
+        const double xx = x[2 * k], xy = x[2 * k + 1];
+        a[0] += ox * xx - oy * xy;
+        a[1] += ox * xy + oy * xx;
+    }
+    blk_sum<2>(a, sh);
+    if (threadIdx.x == 0) { z[2 * s] = a[0]; z[2 * s + 1] = a[1]; }
+}
+
+// y_k = (1/W) sum_s w_s conj(O_sk) z_s - conj(Obar_k) zbar + lambda x_k
+__global__ void k_sr_out(const double *__restrict__ O, const double *__restrict__ z, const double *__restrict__ w,
+                         const double *__restrict__ zst, const double *__restrict__ x, double lambda, int64_t n,
+                         int64_t P, double *__restrict__ y, const double *__restrict__ state)
+{
+    if (state && state[S_DONE] != 0.0) return;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    double ax = 0, ay = 0, mx = 0, my = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const double ws = w ? w[s] : 1.0;
+        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
+        const double zx = z[2 * s], zy = z[2 * s + 1];
+        ax += ws * (ox * zx + oy * zy);
+        ay += ws * (ox * zy - oy * zx);
+        mx += ws * ox;
+        my += ws * oy;
+    }
+    const double inv = 1.0 / zst[S_W];
+    ax *= inv; ay *= inv; mx *= inv; my *= inv;
+    const double bx = zst[S_MEAN], by = zst[S_MEAN + 1];
+    y[2 * k] = ax - (mx * bx + my * by) + lambda * x[2 * k];
+    y[2 * k + 1] = ay - (mx * by - my * bx) + lambda * x[2 * k + 1];
+}
+
+static void matvec(const double *O, const double *w, int64_t n, int64_t P, const double *x, double lambda, double *y,
+                   double *z, double *zst, const double *state, cudaStream_t st)
+{
+    k_ov<<<(unsigned)n, kSrThreads, 0, st>>>(O, x, P, z, state);
+    k_wmean<<<1, kSrThreads, 0, st>>>(z, w, n, zst);
+    k_sr_out<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(O, z, w, zst, x, lambda, n, P, y, state);
+}
+
+cudaError_t launch_sr_matvec(const double *O, const double *w, int64_t n, int64_t P, const double *x, double lambda,
+                             double *y, double *scratch, cudaStream_t st)
+{
+    double *zst = scratch;                                     // its own small state block
+    double *z = scratch + kStateDoubles + 2 * kDotBlocks;
+    matvec(O, w, n, P, x, lambda, y, z, zst, nullptr, st);
+    return cudaGetLastError();
+}
+
+// ---- conjugate gradients --------------------------------------------------
+__global__ void __launch_bounds__(kSrThreads) k_dot_partial(const double *__restrict__ a, const double *__restrict__ b,
+                                                            int64_t P, double *__restrict__ part)
+{
+    __shared__ double sh[kSrThreads / 32][1];
+    double v[1] = {0};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
+        v[0] += a[2 * k] * b[2 * k] + a[2 * k + 1] * b[2 * k + 1];   // Re(conj(a) b)
+    blk_sum<1>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+// mode 0: start (rr = |b|^2), 1: pAp -> alpha, 2: rr_new -> beta, convergence
+__global__ void k_dot_final(const double *__restrict__ part, int nb, double *__restrict__ state, int mode, double tol)
+{
+    if (threadIdx.x != 0) return;
+    double s = 0;
+    for (int i = 0; i < nb; ++i) s += part[i];
+    if (mode == 0) {
+        state[S_RR] = s; state[S_B2] = s; state[S_IT] = 0; state[S_ALPHA] = 0; state[S_BETA] = 0;
+        state[S_DONE] = (s == 0.0) ? 1.0 : 0.0;
+    } else if (mode == 1) {
+        state[S_PAP] = s;
+        state[S_ALPHA] = (state[S_DONE] != 0.0 || s == 0.0) ? 0.0 : state[S_RR] / s;
+    } else {
+        if (state[S_DONE] != 0.0) return;
+        state[S_BETA] = state[S_RR] > 0 ? s / state[S_RR] : 0.0;
+        state[S_RR] = s;
+        state[S_IT] += 1.0;
+        if (sqrt(s) <= tol * sqrt(state[S_B2])) state[S_DONE] = 1.0;
+    }
+}
+
+__global__ void k_cg_init(const double *__restrict__ F, double dtau, int64_t P, double *__restrict__ x,
+                          double *__restrict__ r, double *__restrict__ p)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const double bx = -dtau * F[2 * k], by = -dtau * F[2 * k + 1];
+    x[2 * k] = 0; x[2 * k + 1] = 0;
+    r[2 * k] = bx; r[2 * k + 1] = by;
+    p[2 * k] = bx; p[2 * k + 1] = by;
+}
+
+__global__ void k_cg_update(int64_t P, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                            const double *__restrict__ Ap, const double *__restrict__ state)
+{
+    if (state[S_DONE] != 0.0) return;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const double a = state[S_ALPHA];
+    x[2 * k] += a * p[2 * k]; x[2 * k + 1] += a * p[2 * k + 1];
+    r[2 * k] -= a * Ap[2 * k]; r[2 * k + 1] -= a * Ap[2 * k + 1];
+}
+
+__global__ void k_cg_dir(int64_t P, const double *__restrict__ r, double *__restrict__ p, const double *__restrict__ state)
+{
+    if (state[S_DONE] != 0.0) return;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const double b = state[S_BETA];
+    p[2 * k] = r[2 * k] + b * p[2 * k];
+    p[2 * k + 1] = r[2 * k + 1] + b * p[2 * k + 1];
+}
+
+__global__ void k_cg_finish(int64_t P, const double *__restrict__ x, double *__restrict__ params,
+                            const double *__restrict__ state, double *__restrict__ info)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (params && k < P) { params[2 * k] += x[2 * k]; params[2 * k + 1] += x[2 * k + 1]; }
+    if (info && k == 0) {
+        info[0] = state[S_IT];
+        info[1] = state[S_B2] > 0 ? sqrt(state[S_RR] / state[S_B2]) : 0.0;
+    }
+}
+
+cudaError_t launch_sr_solve(const double *O, const double *w, int64_t n, int64_t P, const double *F, double lambda,
+                            double dtau, int max_iter, double tol, double *x, double *info, double *params_inout,
+                            double *scratch, cudaStream_t st)
+{
+    double *state = scratch;
+    double *part = scratch + kStateDoubles;
+    double *z = part + 2 * kDotBlocks;
+    double *r = z + 2 * n, *p = r + 2 * P, *Ap = p + 2 * P;
+    double *zst = Ap + 2 * P;   // state block of the matvec means (16 doubles)
+    const unsigned gp = (unsigned)((P + 255) / 256);
+    k_cg_init<<<gp, 256, 0, st>>>(F, dtau, P, x, r, p);
+    k_dot_partial<<<kDotBlocks, kSrThreads, 0, st>>>(r, r, P, part);
+    k_dot_final<<<1, 32, 0, st>>>(part, kDotBlocks, state, 0, tol);
+    for (int it = 0; it < max_iter; ++it) {
+        matvec(O, w, n, P, p, lambda, Ap, z, zst, state, st);
+        k_dot_partial<<<kDotBlocks, kSrThreads, 0, st>>>(p, Ap, P, part);
+        k_dot_final<<<1, 32, 0, st>>>(part, kDotBlocks, state, 1, tol);
+        k_cg_update<<<gp, 256, 0, st>>>(P, x, r, p, Ap, state);
+        k_dot_partial<<<kDotBlocks, kSrThreads, 0, st>>>(r, r, P, part);
+        k_dot_final<<<1, 32, 0, st>>>(part, kDotBlocks, state, 2, tol);
+        k_cg_dir<<<gp, 256, 0, st>>>(P, r, p, state);
+    }
+    k_cg_finish<<<gp, 256, 0, st>>>(P, x, params_inout, state, info);
+    return cudaGetLastError();
+}
+
+}  // namespace nnqs

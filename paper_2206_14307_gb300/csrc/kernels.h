@@ -43,10 +43,15 @@ cudaError_t launch_moments(const double *h1, const double *h2, int64_t n, double
                            double *moments, double *lanczos, cudaStream_t st);
 cudaError_t launch_eloc_sums(const double *eloc, int64_t n, double *partial, int nblocks, double *sums,
                              cudaStream_t st);
-cudaError_t launch_energy_grad(const double *O, const double *eloc, int64_t n, int64_t P, double *F, double *scratch,
-                               cudaStream_t st);
-cudaError_t launch_sr_matvec(const double *O, int64_t n, int64_t P, const double *x, double lambda, double *y,
-                             double *scratch, cudaStream_t st);
+// SR pieces (Eq. 12), all in FP64; weights may be NULL (plain sample means)
+size_t sr_scratch_doubles(int64_t n, int64_t P);
+cudaError_t launch_energy_grad(const double *O, const double *eloc, const double *w, int64_t n, int64_t P, double *F,
+                               double *scratch, cudaStream_t st);
+cudaError_t launch_sr_matvec(const double *O, const double *w, int64_t n, int64_t P, const double *x, double lambda,
+                             double *y, double *scratch, cudaStream_t st);
+cudaError_t launch_sr_solve(const double *O, const double *w, int64_t n, int64_t P, const double *F, double lambda,
+                            double dtau, int max_iter, double tol, double *x, double *info, double *params_inout,
+                            double *scratch, cudaStream_t st);
 
 // parameter-derived tables
 template <typename T>

@@ -27,7 +27,7 @@ ABI_FUNCTIONS = (
     "nnqs_create", "nnqs_destroy", "nnqs_num_params", "nnqs_group_size", "nnqs_set_params",
     "nnqs_set_params_device", "nnqs_sample", "nnqs_log_psi", "nnqs_local_energy",
     "nnqs_lanczos_moments", "nnqs_grad_logpsi", "nnqs_energy_grad", "nnqs_sr_matvec",
-    "nnqs_status", "nnqs_last_error", "nnqs_lanczos_moments_noalloc",
+    "nnqs_status", "nnqs_last_error", "nnqs_lanczos_moments_noalloc", "nnqs_sr_solve",
 )
 NOALLOC_MAX_SAMPLES = 65536
 
@@ -71,8 +71,9 @@ def lib():
             "nnqs_local_energy": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_lanczos_moments": ([P, P, i64, P, P, P, P, P], ctypes.c_int),
             "nnqs_grad_logpsi": ([P, P, i64, P, P], ctypes.c_int),
-            "nnqs_energy_grad": ([P, P, P, i64, P, P], ctypes.c_int),
-            "nnqs_sr_matvec": ([P, P, i64, P, d, P, P], ctypes.c_int),
+            "nnqs_energy_grad": ([P, P, P, P, i64, P, P], ctypes.c_int),
+            "nnqs_sr_matvec": ([P, P, P, i64, P, d, P, P], ctypes.c_int),
+            "nnqs_sr_solve": ([P, P, P, i64, P, d, d, i32, d, P, P, P, P], ctypes.c_int),
             "nnqs_status": ([P, P], ctypes.c_int),
             "nnqs_lanczos_moments_noalloc": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_last_error": ([], ctypes.c_char_p),
@@ -118,8 +119,17 @@ def nnqs_lanczos_moments(h, cfg, n, h1, h2, moments, lanczos, stream=0):
 
 
 def nnqs_grad_logpsi(h, cfg, n, O, stream=0): return _check(lib().nnqs_grad_logpsi(h, cfg, n, O, stream))
-def nnqs_energy_grad(h, O, eloc, n, F, stream=0): return _check(lib().nnqs_energy_grad(h, O, eloc, n, F, stream))
-def nnqs_sr_matvec(h, O, n, x, lam, y, stream=0): return _check(lib().nnqs_sr_matvec(h, O, n, x, lam, y, stream))
+def nnqs_energy_grad(h, O, eloc, weights, n, F, stream=0):
+    return _check(lib().nnqs_energy_grad(h, O, eloc, weights, n, F, stream))
+
+
+def nnqs_sr_matvec(h, O, weights, n, x, lam, y, stream=0):
+    return _check(lib().nnqs_sr_matvec(h, O, weights, n, x, lam, y, stream))
+
+
+def nnqs_sr_solve(h, O, weights, n, F, lam, dtau, max_iter, tol, delta, info, params_inout, stream=0):
+    return _check(lib().nnqs_sr_solve(h, O, weights, n, F, lam, dtau, max_iter, tol, delta, info, params_inout,
+                                      stream))
 def nnqs_status(h, stream=0): return _check(lib().nnqs_status(h, stream))
 
 
@@ -218,17 +228,26 @@ class Model:
         nnqs_grad_logpsi(self.h, cfg.data_ptr(), n, out.data_ptr(), _stream())
         return out
 
-    def energy_grad(self, O, eloc, out=None):
+    def energy_grad(self, O, eloc, out=None, weights=None):
         n = O.shape[0]
         out = self._out(self.P, 2) if out is None else out
-        nnqs_energy_grad(self.h, O.data_ptr(), eloc.data_ptr(), n, out.data_ptr(), _stream())
+        nnqs_energy_grad(self.h, O.data_ptr(), eloc.data_ptr(), _ptr(weights), n, out.data_ptr(), _stream())
         return out
 
-    def sr_matvec(self, O, x, lam, out=None):
+    def sr_matvec(self, O, x, lam, out=None, weights=None):
         n = O.shape[0]
         out = self._out(self.P, 2) if out is None else out
-        nnqs_sr_matvec(self.h, O.data_ptr(), n, x.data_ptr(), float(lam), out.data_ptr(), _stream())
+        nnqs_sr_matvec(self.h, O.data_ptr(), _ptr(weights), n, x.data_ptr(), float(lam), out.data_ptr(), _stream())
         return out
+
+    def sr_solve(self, O, F, lam=1e-6, dtau=1.0, max_iter=200, tol=1e-10, weights=None, params_inout=None):
+        """CG solution of (S + lam) delta = -dtau F; returns (delta, info)."""
+        n = O.shape[0]
+        delta = self._out(self.P, 2)
+        info = self._out(2)
+        nnqs_sr_solve(self.h, O.data_ptr(), _ptr(weights), n, F.data_ptr(), float(lam), float(dtau), int(max_iter),
+                      float(tol), delta.data_ptr(), info.data_ptr(), _ptr(params_inout), _stream())
+        return delta, info
 
     def status(self):
         return nnqs_status(self.h, _stream())
