@@ -223,6 +223,75 @@ int nnqs_sr_solve(const nnqs_model *model, const double *O, const double *weight
 int nnqs_lanczos_moments_noalloc(nnqs_model *model, const uint64_t *cfg, int64_t n, double *moments_out,
                                  double *lanczos_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Mixed batch: instances of uneven size in one persistent launch.
+ *
+ * A batch owns n_models independent models (each with its own L, J1, J2, K, M,
+ * projection and parameters).  nnqs_batch_lanczos computes, for every
+ * instance, h1 = (H psi)/psi and h2 = (H^2 psi)/psi at its configurations and
+ * the FP64 moments and p = 1 Lanczos step of nnqs_lanczos_moments (Sec. 3.3,
+ * Eqs. 13-17), all instances in ONE persistent kernel launch plus one
+ * reduction launch, replayed from a captured CUDA graph.  Each instance runs
+ * with its own tile shape of the connected-configuration engine (GL lanes
+ * per row of the projected sum x MPL hidden units per lane), chosen by
+ * nnqs_batch_autotune or set by nnqs_batch_set_shape.  The paper has no
+ * counterpart (it runs one model at a time): this is the batched form of the
+ * Lanczos step.
+ *
+ * Layout shared by the batch calls: n_per_model is a HOST array [n_models] of
+ * sample counts n_i >= 0; cfg holds the configurations of instance 0, then
+ * instance 1, ..., each n_i x ceil(N_i/64) words; h1_out / h2_out are
+ * [sum n_i][2] in the same order; moments_out is [n_models][8] and
+ * lanczos_out [n_models][3] with the per-model layout of
+ * nnqs_lanczos_moments.  The FP32 engine only: an FP64 instance gives
+ * NNQS_EUNSUPPORTED.
+ * ------------------------------------------------------------------------- */
+typedef struct nnqs_batch nnqs_batch;
+
+/* Number of tile shapes, and shape v's GL (lanes per row) and MPL (hidden
+ * units per lane); its width is GL * MPL >= M of an instance that uses it. */
+int32_t nnqs_num_tile_shapes(void);
+int nnqs_tile_shape(int32_t v, int32_t *gl, int32_t *mpl);
+
+/* Creates n_models >= 1 instances from descs (host array) on the current
+ * device; parameters start at zero (set them through nnqs_batch_model).  Each
+ * instance starts with the narrowest tile shape that holds its M. */
+int nnqs_batch_create(const nnqs_desc *descs, int32_t n_models, nnqs_batch **out);
+int nnqs_batch_destroy(nnqs_batch *batch);
+int32_t nnqs_batch_size(const nnqs_batch *batch);
+
+/* Borrowed handle of instance i (owned by the batch; never destroy it): use
+ * it with every single-model call, e.g. nnqs_set_params or nnqs_sample. */
+nnqs_model *nnqs_batch_model(nnqs_batch *batch, int32_t i);
+
+/* Tile shape of instance i (-1 if i is out of range); setting one that does
+ * not fit the instance's width gives NNQS_EINVAL.  Synchronises the device. */
+int32_t nnqs_batch_get_shape(const nnqs_batch *batch, int32_t i);
+int nnqs_batch_set_shape(nnqs_batch *batch, int32_t i, int32_t v);
+
+/* Autotuner: for every instance with more than one candidate shape (widths up
+ * to 15% above the narrowest that holds M), times the persistent kernel on
+ * one full wave of that instance's first min(n_i, probe) configurations with
+ * each candidate (CUDA events on stream) and keeps the fastest; instances of
+ * the same size (N, M, |G|, inversion, bias) share one result.  Host outputs
+ * (may be NULL): shape_out [n_models], ms_out [n_models] (the winning wave
+ * time, 0 where nothing was timed).  Blocks until done. */
+int nnqs_batch_autotune(nnqs_batch *batch, const uint64_t *cfg, const int64_t *n_per_model, int32_t probe,
+                        int32_t *shape_out, double *ms_out, void *stream);
+
+/* One Lanczos step of every instance (layout above).  h1_out, h2_out,
+ * moments_out, lanczos_out may each be NULL (h1/h2 then live in the batch's
+ * workspace).  The first call with a given set of pointers and counts builds
+ * the work list (instances in decreasing per-sample work), copies it to the
+ * device (synchronising the stream) and captures the launches as a CUDA
+ * graph; later calls with the same arguments only replay the graph on
+ * stream.  Calls on one batch must not overlap on the GPU. */
+int nnqs_batch_lanczos(nnqs_batch *batch, const uint64_t *cfg, const int64_t *n_per_model, double *h1_out,
+                       double *h2_out, double *moments_out, double *lanczos_out, void *stream);
+
+/* nnqs_status over every instance: the first non-OK status, else NNQS_OK. */
+int nnqs_batch_status(nnqs_batch *batch, void *stream);
+
 /* Device status word: NNQS_OK, or NNQS_ERANGE if a kernel produced a
  * non-finite amplitude since the last call.  Synchronises the stream and
  * clears the word. */

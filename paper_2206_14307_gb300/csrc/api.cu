@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/nnqs.h: argument validation, host-side
 // lattice and symmetry tables (Sec. 2.1 Eq. 1, Sec. 3.1 Eqs. 4-6), device
 // memory of the model, and dispatch to the kernels.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -111,6 +112,7 @@ int make_group(const nnqs_desc &d, std::vector<uint8_t> &perm, std::vector<doubl
 struct nnqs_model {
     nnqs_desc d;
     int N, G, nsign, nwords, nbonds, nsm, device;
+    int Mp;  // row stride of the connected-configuration tables
     int64_t P;
     bool fp64;
     uint8_t *perm = nullptr;
@@ -136,7 +138,7 @@ template <typename T> DevModel<T> view(const nnqs_model *m)
 {
     DevModel<T> v;
     v.L = m->d.L; v.N = m->N; v.K = m->d.K; v.M = m->d.M; v.G = m->G; v.nsign = m->nsign;
-    v.Mp = conn_mpad(m->d.M);
+    v.Mp = m->Mp;
     v.use_bias = m->d.use_bias; v.nbonds = m->nbonds; v.nwords = m->nwords; v.chiP = m->d.spin_inversion;
     v.J1 = (T)m->d.J1; v.J2 = (T)m->d.J2;
     v.perm = m->perm; v.chi = (const T *)m->chi;
@@ -192,7 +194,9 @@ extern "C" {
 
 const char *nnqs_last_error(void) { return g_err.c_str(); }
 
-int nnqs_create(const nnqs_desc *desc, nnqs_model **out)
+// mp_min: smallest row stride of the connected-configuration tables (0: the
+// narrowest that the model's width allows)
+static int create_model(const nnqs_desc *desc, int mp_min, nnqs_model **out)
 {
     if (!desc || !out) return fail(NNQS_EINVAL, "desc and out must be non-NULL");
     *out = nullptr;
@@ -216,6 +220,7 @@ int nnqs_create(const nnqs_desc *desc, nnqs_model **out)
     m->nsign = d.spin_inversion ? 2 : 1;
     m->P = (int64_t)d.K * (1 + m->N + d.M + (int64_t)d.M * m->N);
     m->fp64 = d.precision == NNQS_FP64;
+    m->Mp = conn_mpad(d.M) > mp_min ? conn_mpad(d.M) : mp_min;
     cudaGetDevice(&m->device);
     cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, m->device);
 
@@ -246,7 +251,7 @@ int nnqs_create(const nnqs_desc *desc, nnqs_model **out)
     ALLOC(m->logc, K * 2 * ts);
     ALLOC(m->X, K * N * M * 4 * ts);
     ALLOC(m->XA, K * N * 4 * ts);
-    const size_t Mp = (size_t)conn_mpad(d.M);
+    const size_t Mp = (size_t)m->Mp;
     ALLOC(m->Tb, K * 2 * bi.size() * Mp * 2 * ts);
     ALLOC(m->Cb, K * bi.size() * 2 * ts);
     ALLOC(m->S4, K * 2 * N * Mp * 2 * ts);
@@ -305,6 +310,8 @@ int nnqs_create(const nnqs_desc *desc, nnqs_model **out)
                                                                            : cleanup(NNQS_ECUDA);
 }
 
+int nnqs_create(const nnqs_desc *desc, nnqs_model **out) { return create_model(desc, 0, out); }
+
 int nnqs_destroy(nnqs_model *m)
 {
     if (!m) return NNQS_OK;
@@ -340,11 +347,11 @@ int nnqs_set_params_device(nnqs_model *m, const double *params, int64_t P, void 
                                            (cx2<float> *)m->XA, st);
         if (e != cudaSuccess) return cuda_fail(e, "build tables");
         if (m->fp64)
-            e = launch_tables_conn<double>(m->params, m->N, m->d.M, m->d.K, m->nbonds, m->d.use_bias, m->bi, m->bj,
+            e = launch_tables_conn<double>(m->params, m->N, m->d.M, m->Mp, m->d.K, m->nbonds, m->d.use_bias, m->bi, m->bj,
                                            (cx<double> *)m->Tb, (cx<double> *)m->Cb, (cx<double> *)m->S4,
                                            (cx<double> *)m->CS, (sc<double> *)m->ES, st);
         else
-            e = launch_tables_conn<float>(m->params, m->N, m->d.M, m->d.K, m->nbonds, m->d.use_bias, m->bi, m->bj,
+            e = launch_tables_conn<float>(m->params, m->N, m->d.M, m->Mp, m->d.K, m->nbonds, m->d.use_bias, m->bi, m->bj,
                                           (cx<float> *)m->Tb, (cx<float> *)m->Cb, (cx<float> *)m->S4,
                                           (cx<float> *)m->CS, (sc<float> *)m->ES, st);
         if (e != cudaSuccess) return cuda_fail(e, "build connection tables");
@@ -612,6 +619,367 @@ int nnqs_status(nnqs_model *m, void *stream)
         if (h) return fail(h, "a kernel produced a non-finite amplitude");
         return NNQS_OK;
     });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Mixed batch: instances of uneven size in one persistent launch
+// ---------------------------------------------------------------------------
+struct nnqs_batch {
+    std::vector<nnqs_model *> models;
+    std::vector<int> shape;     // tile shape of each instance (index into kTileGL / kTileMPL)
+    std::vector<double> cost;   // per-sample work estimate, orders the work list
+    int device = 0, nsm = 0, grid = 0;
+    DevModel<float> *d_models = nullptr;
+    int *d_shape = nullptr, *d_counter = nullptr;
+    int64_t *d_cfg_off = nullptr, *d_out_off = nullptr;
+    BatchItem *d_items = nullptr, *d_titems = nullptr;
+    size_t items_cap = 0, titems_cap = 0;
+    double *d_h = nullptr, *d_th = nullptr;  // h1 | h2 when the caller passes none; tuning outputs
+    size_t h_cap = 0, th_cap = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // arguments the captured graph was built for
+    const uint64_t *k_cfg = nullptr;
+    double *k_h1 = nullptr, *k_h2 = nullptr, *k_mo = nullptr, *k_lz = nullptr;
+    std::vector<int64_t> k_n;
+};
+
+namespace {
+
+int shape_width(int v) { return kTileGL[v] * kTileMPL[v]; }
+
+// Tile shapes an instance of width M may run with: every shape from the
+// narrowest width that holds M up to 15% wider.
+std::vector<int> shape_candidates(int M)
+{
+    int w0 = 1 << 30;
+    for (int v = 0; v < kNumTileShapes; ++v)
+        if (shape_width(v) >= M && shape_width(v) < w0) w0 = shape_width(v);
+    const int wmax = w0 + (w0 * 15 + 99) / 100;
+    std::vector<int> c;
+    for (int v = 0; v < kNumTileShapes; ++v)
+        if (shape_width(v) >= M && shape_width(v) <= wmax) c.push_back(v);
+    return c;
+}
+
+int widest(const std::vector<int> &c)
+{
+    int w = 0;
+    for (int v : c) w = shape_width(v) > w ? shape_width(v) : w;
+    return w;
+}
+
+template <typename P> int grow(P *&p, size_t &cap, size_t n)
+{
+    if (n <= cap) return NNQS_OK;
+    if (p) {
+        cudaDeviceSynchronize();
+        cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    cudaError_t e = cudaMalloc((void **)&p, n * sizeof(P));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NNQS_ENOMEM, "batch buffer of %zu bytes refused", n * sizeof(P));
+    }
+    cap = n;
+    return NNQS_OK;
+}
+
+void drop_graph(nnqs_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->k_n.clear();
+}
+
+int batch_check(const nnqs_batch *b, const uint64_t *cfg, const int64_t *n, int64_t &total)
+{
+    if (!b) return fail(NNQS_EINVAL, "batch is NULL");
+    if (!n) return fail(NNQS_EINVAL, "n_per_model must be non-NULL");
+    total = 0;
+    for (size_t i = 0; i < b->models.size(); ++i) {
+        if (n[i] < 0) return fail(NNQS_EINVAL, "n_per_model[%zu] < 0", i);
+        total += n[i];
+    }
+    if (total > 0x7fffffffLL) return fail(NNQS_EINVAL, "more than 2^31 - 1 samples in one batch");
+    if (total > 0 && !cfg) return fail(NNQS_EINVAL, "cfg must be non-NULL");
+    return NNQS_OK;
+}
+
+void batch_offsets(const nnqs_batch *b, const int64_t *n, std::vector<int64_t> &cfg_off, std::vector<int64_t> &out_off)
+{
+    const size_t nm = b->models.size();
+    cfg_off.assign(nm, 0);
+    out_off.assign(nm + 1, 0);
+    for (size_t i = 0; i < nm; ++i) {
+        if (i) cfg_off[i] = cfg_off[i - 1] + n[i - 1] * b->models[i - 1]->nwords;
+        out_off[i + 1] = out_off[i] + n[i];
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t nnqs_num_tile_shapes(void) { return kNumTileShapes; }
+
+int nnqs_tile_shape(int32_t v, int32_t *gl, int32_t *mpl)
+{
+    if (v < 0 || v >= kNumTileShapes) return fail(NNQS_EINVAL, "tile shape %d out of range", v);
+    if (gl) *gl = kTileGL[v];
+    if (mpl) *mpl = kTileMPL[v];
+    return NNQS_OK;
+}
+
+int nnqs_batch_destroy(nnqs_batch *b)
+{
+    if (!b) return NNQS_OK;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    for (nnqs_model *m : b->models) nnqs_destroy(m);
+    void *ptrs[] = {b->d_models, b->d_shape, b->d_counter, b->d_cfg_off, b->d_out_off,
+                    b->d_items, b->d_titems, b->d_h, b->d_th};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return NNQS_OK;
+}
+
+int nnqs_batch_create(const nnqs_desc *descs, int32_t n_models, nnqs_batch **out)
+{
+    if (!descs || !out) return fail(NNQS_EINVAL, "descs and out must be non-NULL");
+    *out = nullptr;
+    if (n_models < 1) return fail(NNQS_EINVAL, "n_models must be >= 1");
+    for (int i = 0; i < n_models; ++i)
+        if (descs[i].precision == NNQS_FP64)
+            return fail(NNQS_EUNSUPPORTED, "instance %d: the mixed batch runs the FP32 engine (precision FP64)", i);
+    nnqs_batch *b = new nnqs_batch();
+    auto cleanup = [&](int rc) { nnqs_batch_destroy(b); return rc; };
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
+    std::vector<DevModel<float>> views;
+    for (int i = 0; i < n_models; ++i) {
+        const std::vector<int> c = shape_candidates(descs[i].M);
+        nnqs_model *m = nullptr;
+        int rc = create_model(&descs[i], widest(c), &m);
+        if (rc) return cleanup(rc);
+        b->models.push_back(m);
+        b->shape.push_back(c.front());
+        // Lanczos work per sample ~ (pairs of exchanged bonds) x rows x width
+        const double nb = 2.0 * m->N;
+        b->cost.push_back(nb * nb * (double)m->d.K * m->G * m->nsign * shape_width(c.front()));
+        views.push_back(view<float>(m));
+    }
+    b->grid = mixed_grid(b->nsm);
+    if (b->grid <= 0) return cleanup(fail(NNQS_ECUDA, "mixed-batch kernel cannot be resident"));
+#define BALLOC(ptr, count)                                                                       \
+    do {                                                                                         \
+        cudaError_t e_ = cudaMalloc((void **)&(ptr), sizeof(*(ptr)) * (size_t)(count));          \
+        if (e_ != cudaSuccess) { cudaGetLastError(); return cleanup(cuda_fail(e_, "cudaMalloc")); } \
+    } while (0)
+    BALLOC(b->d_models, n_models);
+    BALLOC(b->d_shape, n_models);
+    BALLOC(b->d_counter, 1);
+    BALLOC(b->d_cfg_off, n_models);
+    BALLOC(b->d_out_off, n_models + 1);
+#undef BALLOC
+    cudaError_t e = cudaMemcpy(b->d_models, views.data(), views.size() * sizeof(DevModel<float>), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_shape, b->shape.data(), b->shape.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "batch setup"));
+    *out = b;
+    return NNQS_OK;
+}
+
+int32_t nnqs_batch_size(const nnqs_batch *b) { return b ? (int32_t)b->models.size() : -1; }
+
+nnqs_model *nnqs_batch_model(nnqs_batch *b, int32_t i)
+{
+    if (!b || i < 0 || i >= (int32_t)b->models.size()) {
+        fail(NNQS_EINVAL, "instance index out of range");
+        return nullptr;
+    }
+    return b->models[i];
+}
+
+int32_t nnqs_batch_get_shape(const nnqs_batch *b, int32_t i)
+{
+    if (!b || i < 0 || i >= (int32_t)b->models.size()) return -1;
+    return b->shape[i];
+}
+
+int nnqs_batch_set_shape(nnqs_batch *b, int32_t i, int32_t v)
+{
+    if (!b || i < 0 || i >= (int32_t)b->models.size()) return fail(NNQS_EINVAL, "instance index out of range");
+    if (v < 0 || v >= kNumTileShapes) return fail(NNQS_EINVAL, "tile shape %d out of range", v);
+    const nnqs_model *m = b->models[i];
+    if (shape_width(v) < m->d.M || shape_width(v) > m->Mp)
+        return fail(NNQS_EINVAL, "tile shape %d (width %d) does not fit instance %d (M = %d, table stride %d)", v,
+                    shape_width(v), i, m->d.M, m->Mp);
+    return with_device(m, [&]() -> int {
+        NNQS_CUDA(cudaDeviceSynchronize());
+        NNQS_CUDA(cudaMemcpy(b->d_shape + i, &v, sizeof(int), cudaMemcpyHostToDevice));
+        b->shape[i] = v;
+        return NNQS_OK;
+    });
+}
+
+int nnqs_batch_lanczos(nnqs_batch *b, const uint64_t *cfg, const int64_t *n_per_model, double *h1_out,
+                       double *h2_out, double *moments_out, double *lanczos_out, void *stream)
+{
+    int64_t total = 0;
+    if (int rc = batch_check(b, cfg, n_per_model, total)) return rc;
+    const size_t nm = b->models.size();
+    return with_device(b->models[0], [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        if (!h1_out || !h2_out) {
+            if (int rc = grow(b->d_h, b->h_cap, (size_t)4 * (total > 0 ? total : 1))) return rc;
+        }
+        double *H1 = h1_out ? h1_out : b->d_h;
+        double *H2 = h2_out ? h2_out : b->d_h + 2 * total;
+        const std::vector<int64_t> nv(n_per_model, n_per_model + nm);
+        const bool same = b->exec && b->k_cfg == cfg && b->k_h1 == H1 && b->k_h2 == H2 && b->k_mo == moments_out &&
+                          b->k_lz == lanczos_out && b->k_n == nv;
+        if (!same) {
+            drop_graph(b);
+            std::vector<int64_t> cfg_off, out_off;
+            batch_offsets(b, n_per_model, cfg_off, out_off);
+            // work list: instances in decreasing per-sample work, so that the
+            // longest items are taken first and short ones fill the tail
+            std::vector<int> order(nm);
+            for (size_t i = 0; i < nm; ++i) order[i] = (int)i;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->cost[x] > b->cost[y]; });
+            std::vector<BatchItem> items;
+            items.reserve((size_t)total);
+            for (int i : order)
+                for (int64_t k = 0; k < n_per_model[i]; ++k)
+                    items.push_back(BatchItem{i, (int)k, (int)(out_off[i] + k)});
+            if (int rc = grow(b->d_items, b->items_cap, items.size() > 0 ? items.size() : 1)) return rc;
+            NNQS_CUDA(cudaStreamSynchronize(st));
+            NNQS_CUDA(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+            NNQS_CUDA(cudaMemcpy(b->d_cfg_off, cfg_off.data(), nm * sizeof(int64_t), cudaMemcpyHostToDevice));
+            NNQS_CUDA(cudaMemcpy(b->d_out_off, out_off.data(), (nm + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+            // capture: reset the work counter, the persistent launch, the reduction
+            cudaGraph_t g = nullptr;
+            NNQS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap);
+            if (e == cudaSuccess)
+                e = launch_mixed(b->grid, b->d_models, b->d_shape, b->d_items, (int)total, b->d_counter, cfg,
+                                 b->d_cfg_off, H1, H2, b->cap);
+            if (e == cudaSuccess && (moments_out || lanczos_out))
+                e = launch_moments_batched(H1, H2, b->d_out_off, (int)nm, moments_out, lanczos_out, b->cap);
+            const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                b->exec = nullptr;
+                return cuda_fail(e, "capture of the mixed-batch graph");
+            }
+            b->k_cfg = cfg; b->k_h1 = H1; b->k_h2 = H2; b->k_mo = moments_out; b->k_lz = lanczos_out; b->k_n = nv;
+        }
+        NNQS_CUDA(cudaGraphLaunch(b->exec, st));
+        return NNQS_OK;
+    });
+}
+
+int nnqs_batch_autotune(nnqs_batch *b, const uint64_t *cfg, const int64_t *n_per_model, int32_t probe,
+                        int32_t *shape_out, double *ms_out, void *stream)
+{
+    int64_t total = 0;
+    if (int rc = batch_check(b, cfg, n_per_model, total)) return rc;
+    if (probe < 1) return fail(NNQS_EINVAL, "probe must be >= 1");
+    const size_t nm = b->models.size();
+    return with_device(b->models[0], [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        std::vector<int64_t> cfg_off, out_off;
+        batch_offsets(b, n_per_model, cfg_off, out_off);
+        const int R = b->grid;  // one item per resident CTA: a full-load wave
+        if (int rc = grow(b->d_titems, b->titems_cap, (size_t)R)) return rc;
+        if (int rc = grow(b->d_th, b->th_cap, (size_t)4 * R)) return rc;
+        NNQS_CUDA(cudaStreamSynchronize(st));
+        NNQS_CUDA(cudaMemcpy(b->d_cfg_off, cfg_off.data(), nm * sizeof(int64_t), cudaMemcpyHostToDevice));
+        cudaEvent_t e0, e1;
+        NNQS_CUDA(cudaEventCreate(&e0));
+        NNQS_CUDA(cudaEventCreate(&e1));
+        struct Done { int N, M, G, nsign, bias, shape; double ms; };
+        std::vector<Done> done;  // instances of the same size share a result
+        // tune the smallest-K instance of each size first
+        std::vector<int> order(nm);
+        for (size_t i = 0; i < nm; ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return b->models[x]->d.K < b->models[y]->d.K; });
+        std::vector<double> ms(nm, 0.0);
+        int rc = NNQS_OK;
+        for (int i : order) {
+            const nnqs_model *m = b->models[i];
+            const std::vector<int> cand = shape_candidates(m->d.M);
+            if (cand.size() == 1) b->shape[i] = cand.front();
+            if (cand.size() == 1 || n_per_model[i] == 0) continue;
+            bool reused = false;
+            for (const Done &d : done)
+                if (d.N == m->N && d.M == m->d.M && d.G == m->G && d.nsign == m->nsign && d.bias == m->d.use_bias) {
+                    b->shape[i] = d.shape; ms[i] = d.ms; reused = true;
+                    break;
+                }
+            if (reused) continue;
+            const int ns = (int)(n_per_model[i] < probe ? n_per_model[i] : probe);
+            std::vector<BatchItem> items(R);
+            for (int k = 0; k < R; ++k) items[k] = BatchItem{i, k % ns, k};
+            cudaError_t e = cudaMemcpy(b->d_titems, items.data(), R * sizeof(BatchItem), cudaMemcpyHostToDevice);
+            double best = 1e300;
+            int best_v = cand.front();
+            for (int v : cand) {
+                if (e != cudaSuccess) break;
+                e = cudaMemcpy(b->d_shape + i, &v, sizeof(int), cudaMemcpyHostToDevice);
+                double t_min = 1e300;
+                for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                    e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                    if (e == cudaSuccess)
+                        e = launch_mixed(b->grid, b->d_models, b->d_shape, b->d_titems, R, b->d_counter, cfg,
+                                         b->d_cfg_off, b->d_th, b->d_th + 2 * R, st);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float t = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                    if (e != cudaSuccess) break;
+                    if (rep > 0 || t > 50.f) t_min = t < t_min ? t : t_min;  // first run warms up short ones
+                    if (t > 50.f) break;                                     // long runs: one is enough
+                }
+                if (t_min < best) { best = t_min; best_v = v; }
+            }
+            if (e != cudaSuccess) { rc = cuda_fail(e, "autotune"); break; }
+            b->shape[i] = best_v;
+            ms[i] = best;
+            done.push_back(Done{m->N, m->d.M, m->G, m->nsign, m->d.use_bias, best_v, best});
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        NNQS_CUDA(cudaMemcpy(b->d_shape, b->shape.data(), nm * sizeof(int), cudaMemcpyHostToDevice));
+        for (size_t i = 0; i < nm; ++i) {
+            if (shape_out) shape_out[i] = b->shape[i];
+            if (ms_out) ms_out[i] = ms[i];
+        }
+        return NNQS_OK;
+    });
+}
+
+int nnqs_batch_status(nnqs_batch *b, void *stream)
+{
+    if (!b) return fail(NNQS_EINVAL, "batch is NULL");
+    int worst = NNQS_OK;
+    for (nnqs_model *m : b->models) {
+        const int rc = nnqs_status(m, stream);
+        if (rc != NNQS_OK && worst == NNQS_OK) worst = rc;
+    }
+    return worst;
 }
 
 }  // extern "C"

@@ -200,17 +200,46 @@ __device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 // ---------------------------------------------------------------------------
 // Device view of a model (passed by value to kernels)
 // ---------------------------------------------------------------------------
-// Row stride of the connected-configuration tables: M padded to the
-// (lanes per row) x (units per lane) tiling of the kernel variant, with neutral
-// entries (T = 0, e^{+-4W} = 1) past M so that the inner loops need no bound.
-__host__ __device__ __forceinline__ int conn_mpad(int M)
+// Tile variants of the connected-configuration engine: GL lanes per row x MPL
+// hidden units per lane (width GL * MPL); the one used for a width M is the
+// narrowest that holds it.
+constexpr int kNumVariants = 7;
+__host__ __device__ __forceinline__ int variant_width(int v)
 {
-    return M <= 16 ? 16 : M <= 32 ? 32 : M <= 72 ? 72 : M <= 128 ? 128 : M <= 256 ? 256 : M <= 416 ? 416 : 512;
+    return v == 0 ? 16 : v == 1 ? 32 : v == 2 ? 72 : v == 3 ? 128 : v == 4 ? 256 : v == 5 ? 416 : 512;
+}
+__host__ __device__ __forceinline__ int default_variant(int M)
+{
+    int v = 0;
+    while (v < kNumVariants - 1 && variant_width(v) < M) ++v;
+    return v;
+}
+// Smallest row stride of the connected-configuration tables: M padded to the
+// width of its variant, with neutral entries (T = 0, e^{+-4W} = 1) past M so
+// that the inner loops need no bound.  A model may use a larger stride.
+__host__ __device__ __forceinline__ int conn_mpad(int M) { return variant_width(default_variant(M)); }
+
+// p = 1 Lanczos step from the normalised moments m1, m2, m3 (Sec. 3.3, Eqs.
+// 15-17): the lowest eigenpair of H in span{psi0, psi1}.  out = {E, v, alpha}
+// with v^2 = m2 - m1^2, d = (m3 - 3 m1 m2 + 2 m1^3) / (2 v^3),
+// alpha = d - sqrt(d^2 + 1), E = m1 + v alpha; an exact eigenstate
+// (v^2 <= 1e-14 m1^2) gives E = m1, alpha = 0.
+__device__ __forceinline__ void lanczos_p1(double m1, double m2, double m3, double *out)
+{
+    const double v2 = m2 - m1 * m1;
+    if (v2 <= 1e-14 * m1 * m1 || v2 <= 0.0) {
+        out[0] = m1; out[1] = v2 > 0.0 ? sqrt(v2) : 0.0; out[2] = 0.0;
+    } else {
+        const double vv = sqrt(v2);
+        const double d = (m3 - 3.0 * m1 * m2 + 2.0 * m1 * m1 * m1) / (2.0 * v2 * vv);
+        const double al = d - sqrt(d * d + 1.0);
+        out[0] = m1 + vv * al; out[1] = vv; out[2] = al;
+    }
 }
 
 template <typename T> struct DevModel {
     int L, N, K, M, G, nsign, use_bias, nbonds, nwords, chiP;
-    int Mp;                 // row stride of Tb and S4 (conn_mpad(M))
+    int Mp;                 // row stride of Tb and S4 (>= conn_mpad(M))
     T J1, J2;
     const uint8_t *perm;    // [G][N]   image of site i under g
     const T *chi;           // [G]      +-1

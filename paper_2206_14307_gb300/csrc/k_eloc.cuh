@@ -212,24 +212,29 @@ template <typename T> __device__ __forceinline__ void split(cx<T> pr, T &x, T &y
     }
 }
 
+// Per-CTA state of the connected-configuration engine for one sample.
+template <typename T> struct EShared {
+    T s_sm[kMaxN];
+    int8_t s8[kMaxN];
+    int16_t aa[4 * kMaxN];
+    int n_aa, n_ent, cursor, first_over;
+    int wcount[kWarps];
+    sc<T> wacc0[kWarps];
+    sc<T> S0;
+    double red[kWarps][4];
+    double Hs[4];
+    T diag_sh, cst_sh;
+};
+
+// h1 (and, for MODE 1, h2) of one sample: cfg_row = its configuration words,
+// h1o / h2o = its two output doubles (may be NULL).  Called by every thread of
+// the CTA; smem_raw holds the entries, the accumulators and the tiles.
 template <typename T, int GL, int MPL, int MODE>
-__global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
-                                                   int chunk, double *__restrict__ h1_out, double *__restrict__ h2_out)
+__device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_t *__restrict__ cfg_row, int chunk,
+                                            double *h1o, double *h2o, EShared<T> &S, unsigned char *smem_raw)
 {
     constexpr int mode = MODE;
     constexpr int NG = 32 / GL;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T s_sm[kMaxN];
-    __shared__ int8_t s8[kMaxN];
-    __shared__ int16_t aa[4 * kMaxN];
-    __shared__ int n_aa, n_ent, cursor, first_over;
-    __shared__ int wcount[kWarps];
-    __shared__ sc<T> wacc0[kWarps];
-    __shared__ sc<T> S0;
-    __shared__ double red[kWarps][4];
-    __shared__ double Hs[4];
-    __shared__ T diag_sh, cst_sh;
-
     Entry2<T> *ent = reinterpret_cast<Entry2<T> *>(smem_raw);
     sc<T> *acc = reinterpret_cast<sc<T> *>(smem_raw + sizeof(Entry2<T>) * chunk);  // [kWarps][chunk]
     // transpose tiles of the partial products: [kWarps][TQ][33], TQ = GL (8 for GL = 32)
@@ -243,338 +248,346 @@ __global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_
     const int rows = md.K * md.G;
     const int nb = md.nbonds, N = md.N, M = md.M;
     const int slot = warp * NG + grp, nslots = kWarps * NG;
-
-    for (int64_t smp = blockIdx.x; smp < n; smp += gridDim.x) {
-        {
-            const uint64_t *w = cfg + smp * md.nwords;
-            for (int i = threadIdx.x; i < N; i += blockDim.x) {
-                const int sv = spin_of(w, i);
-                s_sm[i] = T(sv);
-                s8[i] = (int8_t)sv;
-            }
+    {
+        const uint64_t *w = cfg_row;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int sv = spin_of(w, i);
+            S.s_sm[i] = T(sv);
+            S.s8[i] = (int8_t)sv;
         }
-        __syncthreads();
-        if (warp == 0) {
-            T d = T(0), c = T(0);
-            int base = 0;
-            for (int b0 = 0; b0 < nb; b0 += 32) {
-                const int b = b0 + lane;
-                bool isaa = false;
-                if (b < nb) {
-                    const int si = s8[md.bond_i[b]], sj = s8[md.bond_j[b]];
-                    const T J = bondJ(md, b);
-                    d += T(0.25) * J * T(si * sj);
-                    isaa = si != sj;
-                    if (isaa) c += T(0.25) * J * J;
-                }
-                const unsigned bm = __ballot_sync(0xffffffffu, isaa);
-                if (isaa) aa[base + __popc(bm & ((1u << lane) - 1u))] = (int16_t)b;
-                base += __popc(bm);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        T d = T(0), c = T(0);
+        int base = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            bool isaa = false;
+            if (b < nb) {
+                const int si = S.s8[md.bond_i[b]], sj = S.s8[md.bond_j[b]];
+                const T J = bondJ(md, b);
+                d += T(0.25) * J * T(si * sj);
+                isaa = si != sj;
+                if (isaa) c += T(0.25) * J * J;
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                d += __shfl_xor_sync(0xffffffffu, d, o);
-                c += __shfl_xor_sync(0xffffffffu, c, o);
-            }
-            if (lane == 0) { diag_sh = d; cst_sh = c; n_aa = base; cursor = 0; }
+            const unsigned bm = __ballot_sync(0xffffffffu, isaa);
+            if (isaa) S.aa[base + __popc(bm & ((1u << lane) - 1u))] = (int16_t)b;
+            base += __popc(bm);
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) { S.diag_sh = d; S.cst_sh = c; S.n_aa = base; S.cursor = 0; }
+    }
+    __syncthreads();
+    const int ncand = mode == 0 ? nb : S.n_aa * (nb + 1);
+    bool first_chunk = true;
+    while (true) {
+        // ---- gather up to `chunk` entries in candidate order ----
+        if (threadIdx.x == 0) S.n_ent = 0;
         __syncthreads();
-        const int ncand = mode == 0 ? nb : n_aa * (nb + 1);
-        bool first_chunk = true;
         while (true) {
-            // ---- gather up to `chunk` entries in candidate order ----
-            if (threadIdx.x == 0) n_ent = 0;
+            const int cur = S.cursor;
+            if (cur >= ncand || S.n_ent >= chunk) break;
+            const int q = cur + threadIdx.x;
+            Entry2<T> e;
+            const bool valid = q < ncand && candidate2(md, mode, q, S.s8, S.aa, S.diag_sh, e);
+            const unsigned bm = __ballot_sync(0xffffffffu, valid);
+            if (lane == 0) S.wcount[warp] = __popc(bm);
+            if (threadIdx.x == 0) S.first_over = INT_MAX;
             __syncthreads();
-            while (true) {
-                const int cur = cursor;
-                if (cur >= ncand || n_ent >= chunk) break;
-                const int q = cur + threadIdx.x;
-                Entry2<T> e;
-                const bool valid = q < ncand && candidate2(md, mode, q, s8, aa, diag_sh, e);
-                const unsigned bm = __ballot_sync(0xffffffffu, valid);
-                if (lane == 0) wcount[warp] = __popc(bm);
-                if (threadIdx.x == 0) first_over = INT_MAX;
-                __syncthreads();
-                int pos = __popc(bm & ((1u << lane) - 1u));
-                for (int w = 0; w < warp; ++w) pos += wcount[w];
-                const int room = chunk - n_ent;
-                if (valid) {
-                    if (pos < room) ent[n_ent + pos] = e;
-                    else atomicMin(&first_over, q);
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int tot = 0;
-                    for (int w = 0; w < kWarps; ++w) tot += wcount[w];
-                    n_ent += tot < room ? tot : room;
-                    cursor = first_over != INT_MAX ? first_over : cur + blockDim.x;
-                }
-                __syncthreads();
-            }
-            const int ne = n_ent;
-            if (ne == 0 && !first_chunk) break;
-            for (int idx = threadIdx.x; idx < kWarps * ne; idx += blockDim.x) {
-                const int w = idx / ne, e = idx - w * ne;
-                acc[w * chunk + e] = sc<T>{T(0), T(0), 0};
+            int pos = __popc(bm & ((1u << lane) - 1u));
+            for (int w = 0; w < warp; ++w) pos += S.wcount[w];
+            const int room = chunk - S.n_ent;
+            if (valid) {
+                if (pos < room) ent[S.n_ent + pos] = e;
+                else atomicMin(&S.first_over, q);
             }
             __syncthreads();
+            if (threadIdx.x == 0) {
+                int tot = 0;
+                for (int w = 0; w < kWarps; ++w) tot += S.wcount[w];
+                S.n_ent += tot < room ? tot : room;
+                S.cursor = S.first_over != INT_MAX ? S.first_over : cur + blockDim.x;
+            }
+            __syncthreads();
+        }
+        const int ne = S.n_ent;
+        if (ne == 0 && !first_chunk) break;
+        for (int idx = threadIdx.x; idx < kWarps * ne; idx += blockDim.x) {
+            const int w = idx / ne, e = idx - w * ne;
+            acc[w * chunk + e] = sc<T>{T(0), T(0), 0};
+        }
+        __syncthreads();
 
-            sc<T> a0{T(0), T(0), 0};
-            for (int rbase = 0; rbase < rows; rbase += nslots) {
-                const int row = rbase + slot;
-                const bool active = row < rows;
-                const int r = active ? row / md.G : 0, g = active ? row - (row / md.G) * md.G : 0;
-                // ---- theta' = W_r T_g s for the lane's hidden units ----
-                cx<T> thp[MPL];
+        sc<T> a0{T(0), T(0), 0};
+        for (int rbase = 0; rbase < rows; rbase += nslots) {
+            const int row = rbase + slot;
+            const bool active = row < rows;
+            const int r = active ? row / md.G : 0, g = active ? row - (row / md.G) * md.G : 0;
+            // ---- theta' = W_r T_g s for the lane's hidden units ----
+            cx<T> thp[MPL];
 #pragma unroll
-                for (int j = 0; j < MPL; ++j) thp[j] = cx<T>{T(0), T(0)};
-                const uint8_t *pg = md.perm + (size_t)g * N;
-                const cx<T> *Wr = md.Wt + (size_t)r * N * M;
-                for (int i = 0; i < N; ++i) {
-                    const cx<T> *wk = Wr + (size_t)pg[i] * M;
-                    const T si = s_sm[i];
+            for (int j = 0; j < MPL; ++j) thp[j] = cx<T>{T(0), T(0)};
+            const uint8_t *pg = md.perm + (size_t)g * N;
+            const cx<T> *Wr = md.Wt + (size_t)r * N * M;
+            for (int i = 0; i < N; ++i) {
+                const cx<T> *wk = Wr + (size_t)pg[i] * M;
+                const T si = S.s_sm[i];
 #pragma unroll
-                    for (int j = 0; j < MPL; ++j) {
-                        const int m = gl + GL * j;
-                        if (m < M) { const cx<T> w = wk[m]; thp[j].x += si * w.x; thp[j].y += si * w.y; }
-                    }
+                for (int j = 0; j < MPL; ++j) {
+                    const int m = gl + GL * j;
+                    if (m < M) { const cx<T> w = wk[m]; thp[j].x += si * w.x; thp[j].y += si * w.y; }
                 }
-                cx<T> at{T(0), T(0)};
-                if (md.use_bias) {
-                    const cx<T> *ar = md.avec + (size_t)r * N;
-                    for (int i = gl; i < N; i += GL) { const cx<T> a = ar[pg[i]]; at.x += s_sm[i] * a.x; at.y += s_sm[i] * a.y; }
+            }
+            cx<T> at{T(0), T(0)};
+            if (md.use_bias) {
+                const cx<T> *ar = md.avec + (size_t)r * N;
+                for (int i = gl; i < N; i += GL) { const cx<T> a = ar[pg[i]]; at.x += S.s_sm[i] * a.x; at.y += S.s_sm[i] * a.y; }
 #pragma unroll
-                    for (int o = GL / 2; o > 0; o >>= 1) { at.x += shfl_x(at.x, o); at.y += shfl_x(at.y, o); }
-                }
-                // ---- p_m and the row terms of both signs ----
-                cx<T> p[2][MPL];
-                sc<T> term[2];
+                for (int o = GL / 2; o > 0; o >>= 1) { at.x += shfl_x(at.x, o); at.y += shfl_x(at.y, o); }
+            }
+            // ---- p_m and the row terms of both signs ----
+            cx<T> p[2][MPL];
+            sc<T> term[2];
 #pragma unroll
-                for (int sg = 0; sg < 2; ++sg) {
-                    const int sign = sg ? -1 : 1;
-                    sc<T> prod{T(1), T(0), 0};
-                    const cx<T> *br = md.bvec + (size_t)r * M;
+            for (int sg = 0; sg < 2; ++sg) {
+                const int sign = sg ? -1 : 1;
+                sc<T> prod{T(1), T(0), 0};
+                const cx<T> *br = md.bvec + (size_t)r * M;
 #pragma unroll
-                    for (int j = 0; j < MPL; ++j) {
-                        const int m = gl + GL * j;
-                        if (m < M && sg < md.nsign) {
-                            cx<T> th{sign * thp[j].x, sign * thp[j].y};
-                            if (md.use_bias) { const cx<T> b = br[m]; th.x += b.x; th.y += b.y; }
-                            cx<T> mant; int k;
-                            cosh2(th, mant, k, p[sg][j]);
-                            const cx<T> q = cmul(mk(prod.x, prod.y), mant);
-                            prod = sc<T>{q.x, q.y, prod.e + k};
-                        } else {
-                            p[sg][j] = cx<T>{T(0), T(0)};
-                        }
-                    }
-                    prod = sc_norm(prod);
-#pragma unroll
-                    for (int o = GL / 2; o > 0; o >>= 1) {
-                        sc<T> w{shfl_x(prod.x, o), shfl_x(prod.y, o), __shfl_xor_sync(0xffffffffu, prod.e, o)};
-                        prod = sc_mul(prod, w);
-                    }
-                    if (sg < md.nsign && active) {
-                        const cx<T> lc = md.logc[r];
-                        sc<T> lead = sc_exp(cx<T>{lc.x + sign * at.x, lc.y + sign * at.y});
-                        T c = md.chi[g];
-                        if (sign < 0 && md.chiP < 0) c = -c;
-                        lead.x *= c; lead.y *= c;
-                        term[sg] = sc_mul(prod, sc_norm(lead));
+                for (int j = 0; j < MPL; ++j) {
+                    const int m = gl + GL * j;
+                    if (m < M && sg < md.nsign) {
+                        cx<T> th{sign * thp[j].x, sign * thp[j].y};
+                        if (md.use_bias) { const cx<T> b = br[m]; th.x += b.x; th.y += b.y; }
+                        cx<T> mant; int k;
+                        cosh2(th, mant, k, p[sg][j]);
+                        const cx<T> q = cmul(mk(prod.x, prod.y), mant);
+                        prod = sc<T>{q.x, q.y, prod.e + k};
                     } else {
-                        term[sg] = sc<T>{T(0), T(0), 0};
+                        p[sg][j] = cx<T>{T(0), T(0)};
                     }
                 }
-                if (first_chunk && gl == 0) a0 = sc_add(a0, sc_add(term[0], term[1]));
-
-                // ---- entries, GL at a time ----
-                if constexpr (GL < 32) {
-                    // Rolled loop over the GL entries of a batch: each lane writes its
-                    // partial product (over its hidden units) of entry e0 + q into the
-                    // group's tile; lane gl then multiplies the GL partials of entry
-                    // e0 + gl.  Tile [warp][q][lane], row stride 33 words.
-                    T *bx = tx + warp * GL * 33, *by = ty + warp * GL * 33;
-                    int *be = te + warp * GL * 33;
-                    for (int e0 = 0; e0 < ne; e0 += GL) {
-                        sc<T> mine{T(0), T(0), 0};  // lane gl: contribution of entry e0 + gl
+                prod = sc_norm(prod);
 #pragma unroll
-                        for (int sg = 0; sg < 2; ++sg) {
-                            if (sg >= md.nsign) break;
-#pragma unroll 1
-                            for (int q = 0; q < GL; ++q) {
-                                const int e = e0 + q;
-                                cx<T> pr{T(1), T(0)};
-                                if (e < ne) {
-                                    const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, s8);
-                                    pr = entry_partial<T, GL, MPL, MODE == 0>(md, d, sg, p[sg], gl);
-                                }
-                                T sx, sy;
-                                int ex;
-                                split(pr, sx, sy, ex);
-                                bx[q * 33 + lane] = sx;
-                                by[q * 33 + lane] = sy;
-                                be[q * 33 + lane] = ex;
-                            }
-                            __syncwarp();
-                            cx<T> pr{T(1), T(0)};
-                            int pe = 0;
-#pragma unroll
-                            for (int k = 0; k < GL; ++k) {
-                                const int idx = gl * 33 + grp * GL + k;
-                                pr = cmul(pr, cx<T>{bx[idx], by[idx]});
-                                pe += be[idx];
-                                if ((k & 1) == 1) {   // values are below 2^40: renormalise every two
-                                    T sx, sy;
-                                    int ex;
-                                    split(pr, sx, sy, ex);
-                                    pr = cx<T>{sx, sy};
-                                    pe += ex;
-                                }
-                            }
-                            __syncwarp();
-                            const int e = e0 + gl;
-                            if (e < ne && active) {
-                                const Dec<T> d = decode<T, true>(md, ent[e].code, r, g, s8);
-                                const cx<T> E = sg ? cx<T>{-d.E.x, -d.E.y} : d.E;
-                                const sc<T> c = sc_mul(sc_norm(sc<T>{pr.x, pr.y, pe}), sc_exp(E));
-                                mine = sc_add(mine, sc_mul(c, term[sg]));
-                            }
-                        }
-                        // sum over the warp's groups (they hold the same entry index)
-#pragma unroll
-                        for (int o = GL; o < 32; o <<= 1) {
-                            const sc<T> w{shfl_x(mine.x, o), shfl_x(mine.y, o), __shfl_xor_sync(0xffffffffu, mine.e, o)};
-                            mine = sc_add(mine, w);
-                        }
-                        if (grp == 0 && e0 + gl < ne)
-                            acc[warp * chunk + e0 + gl] = sc_add(acc[warp * chunk + e0 + gl], mine);
-                    }
+                for (int o = GL / 2; o > 0; o >>= 1) {
+                    sc<T> w{shfl_x(prod.x, o), shfl_x(prod.y, o), __shfl_xor_sync(0xffffffffu, prod.e, o)};
+                    prod = sc_mul(prod, w);
+                }
+                if (sg < md.nsign && active) {
+                    const cx<T> lc = md.logc[r];
+                    sc<T> lead = sc_exp(cx<T>{lc.x + sign * at.x, lc.y + sign * at.y});
+                    T c = md.chi[g];
+                    if (sign < 0 && md.chiP < 0) c = -c;
+                    lead.x *= c; lead.y *= c;
+                    term[sg] = sc_mul(prod, sc_norm(lead));
                 } else {
-                    // One row per warp: transpose the lanes' partial products of 8
-                    // entries through shared memory; lane (e, part) multiplies 8 of
-                    // the 32 partials of entry e, two shuffle stages combine the parts.
-                    T *bx = tx + warp * TQ * 33, *by = ty + warp * TQ * 33;
-                    int *be = te + warp * TQ * 33;
-                    const int el = lane & 7, part = lane >> 3;
-                    for (int e0 = 0; e0 < ne; e0 += 8) {
+                    term[sg] = sc<T>{T(0), T(0), 0};
+                }
+            }
+            if (first_chunk && gl == 0) a0 = sc_add(a0, sc_add(term[0], term[1]));
+
+            // ---- entries, GL at a time ----
+            if constexpr (GL < 32) {
+                // Rolled loop over the GL entries of a batch: each lane writes its
+                // partial product (over its hidden units) of entry e0 + q into the
+                // group's tile; lane gl then multiplies the GL partials of entry
+                // e0 + gl.  Tile [warp][q][lane], row stride 33 words.
+                T *bx = tx + warp * GL * 33, *by = ty + warp * GL * 33;
+                int *be = te + warp * GL * 33;
+                for (int e0 = 0; e0 < ne; e0 += GL) {
+                    sc<T> mine{T(0), T(0), 0};  // lane gl: contribution of entry e0 + gl
 #pragma unroll
-                        for (int sg = 0; sg < 2; ++sg) {
-                            if (sg >= md.nsign) break;
+                    for (int sg = 0; sg < 2; ++sg) {
+                        if (sg >= md.nsign) break;
 #pragma unroll 1
-                            for (int q = 0; q < 8; ++q) {
-                                const int e = e0 + q;
-                                cx<T> pr{T(1), T(0)};
-                                if (e < ne) {
-                                    const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, s8);
-                                    pr = entry_partial<T, GL, MPL, MODE == 0>(md, d, sg, p[sg], gl);
-                                }
-                                T sx, sy;
-                                int ex;
-                                split(pr, sx, sy, ex);
-                                bx[q * 33 + lane] = sx;
-                                by[q * 33 + lane] = sy;
-                                be[q * 33 + lane] = ex;
-                            }
-                            __syncwarp();
+                        for (int q = 0; q < GL; ++q) {
+                            const int e = e0 + q;
                             cx<T> pr{T(1), T(0)};
-                            int pe = 0;
-#pragma unroll
-                            for (int l = 0; l < 8; ++l) {
-                                const int idx = el * 33 + part * 8 + l;
-                                pr = cmul(pr, cx<T>{bx[idx], by[idx]});
-                                pe += be[idx];
-                                if ((l & 1) == 1) {   // values are below 2^40: renormalise every two
-                                    T sx, sy;
-                                    int ex;
-                                    split(pr, sx, sy, ex);
-                                    pr = cx<T>{sx, sy};
-                                    pe += ex;
-                                }
+                            if (e < ne) {
+                                const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, S.s8);
+                                pr = entry_partial<T, GL, MPL, MODE == 0>(md, d, sg, p[sg], gl);
                             }
-                            __syncwarp();
+                            T sx, sy;
+                            int ex;
+                            split(pr, sx, sy, ex);
+                            bx[q * 33 + lane] = sx;
+                            by[q * 33 + lane] = sy;
+                            be[q * 33 + lane] = ex;
+                        }
+                        __syncwarp();
+                        cx<T> pr{T(1), T(0)};
+                        int pe = 0;
 #pragma unroll
-                            for (int o = 8; o < 32; o <<= 1) {
-                                const cx<T> w{shfl_x(pr.x, o), shfl_x(pr.y, o)};
-                                pe += __shfl_xor_sync(0xffffffffu, pe, o);
-                                pr = cmul(pr, w);
+                        for (int k = 0; k < GL; ++k) {
+                            const int idx = gl * 33 + grp * GL + k;
+                            pr = cmul(pr, cx<T>{bx[idx], by[idx]});
+                            pe += be[idx];
+                            if ((k & 1) == 1) {   // values are below 2^40: renormalise every two
                                 T sx, sy;
                                 int ex;
                                 split(pr, sx, sy, ex);
                                 pr = cx<T>{sx, sy};
                                 pe += ex;
                             }
-                            const int e = e0 + el;
-                            if (part == 0 && e < ne && active) {
-                                const Dec<T> d = decode<T, true>(md, ent[e].code, r, g, s8);
-                                const cx<T> E = sg ? cx<T>{-d.E.x, -d.E.y} : d.E;
-                                const sc<T> c = sc_mul(sc_norm(sc<T>{pr.x, pr.y, pe}), sc_exp(E));
-                                acc[warp * chunk + e] = sc_add(acc[warp * chunk + e], sc_mul(c, term[sg]));
+                        }
+                        __syncwarp();
+                        const int e = e0 + gl;
+                        if (e < ne && active) {
+                            const Dec<T> d = decode<T, true>(md, ent[e].code, r, g, S.s8);
+                            const cx<T> E = sg ? cx<T>{-d.E.x, -d.E.y} : d.E;
+                            const sc<T> c = sc_mul(sc_norm(sc<T>{pr.x, pr.y, pe}), sc_exp(E));
+                            mine = sc_add(mine, sc_mul(c, term[sg]));
+                        }
+                    }
+                    // sum over the warp's groups (they hold the same entry index)
+#pragma unroll
+                    for (int o = GL; o < 32; o <<= 1) {
+                        const sc<T> w{shfl_x(mine.x, o), shfl_x(mine.y, o), __shfl_xor_sync(0xffffffffu, mine.e, o)};
+                        mine = sc_add(mine, w);
+                    }
+                    if (grp == 0 && e0 + gl < ne)
+                        acc[warp * chunk + e0 + gl] = sc_add(acc[warp * chunk + e0 + gl], mine);
+                }
+            } else {
+                // One row per warp: transpose the lanes' partial products of 8
+                // entries through shared memory; lane (e, part) multiplies 8 of
+                // the 32 partials of entry e, two shuffle stages combine the parts.
+                T *bx = tx + warp * TQ * 33, *by = ty + warp * TQ * 33;
+                int *be = te + warp * TQ * 33;
+                const int el = lane & 7, part = lane >> 3;
+                for (int e0 = 0; e0 < ne; e0 += 8) {
+#pragma unroll
+                    for (int sg = 0; sg < 2; ++sg) {
+                        if (sg >= md.nsign) break;
+#pragma unroll 1
+                        for (int q = 0; q < 8; ++q) {
+                            const int e = e0 + q;
+                            cx<T> pr{T(1), T(0)};
+                            if (e < ne) {
+                                const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, S.s8);
+                                pr = entry_partial<T, GL, MPL, MODE == 0>(md, d, sg, p[sg], gl);
                             }
+                            T sx, sy;
+                            int ex;
+                            split(pr, sx, sy, ex);
+                            bx[q * 33 + lane] = sx;
+                            by[q * 33 + lane] = sy;
+                            be[q * 33 + lane] = ex;
+                        }
+                        __syncwarp();
+                        cx<T> pr{T(1), T(0)};
+                        int pe = 0;
+#pragma unroll
+                        for (int l = 0; l < 8; ++l) {
+                            const int idx = el * 33 + part * 8 + l;
+                            pr = cmul(pr, cx<T>{bx[idx], by[idx]});
+                            pe += be[idx];
+                            if ((l & 1) == 1) {   // values are below 2^40: renormalise every two
+                                T sx, sy;
+                                int ex;
+                                split(pr, sx, sy, ex);
+                                pr = cx<T>{sx, sy};
+                                pe += ex;
+                            }
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int o = 8; o < 32; o <<= 1) {
+                            const cx<T> w{shfl_x(pr.x, o), shfl_x(pr.y, o)};
+                            pe += __shfl_xor_sync(0xffffffffu, pe, o);
+                            pr = cmul(pr, w);
+                            T sx, sy;
+                            int ex;
+                            split(pr, sx, sy, ex);
+                            pr = cx<T>{sx, sy};
+                            pe += ex;
+                        }
+                        const int e = e0 + el;
+                        if (part == 0 && e < ne && active) {
+                            const Dec<T> d = decode<T, true>(md, ent[e].code, r, g, S.s8);
+                            const cx<T> E = sg ? cx<T>{-d.E.x, -d.E.y} : d.E;
+                            const sc<T> c = sc_mul(sc_norm(sc<T>{pr.x, pr.y, pe}), sc_exp(E));
+                            acc[warp * chunk + e] = sc_add(acc[warp * chunk + e], sc_mul(c, term[sg]));
                         }
                     }
                 }
             }
-            if (first_chunk) {
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const sc<T> w{shfl_x(a0.x, o), shfl_x(a0.y, o), __shfl_xor_sync(0xffffffffu, a0.e, o)};
-                    a0 = sc_add(a0, w);
-                }
-                if (lane == 0) wacc0[warp] = a0;
-            }
-            __syncthreads();
-            if (first_chunk && threadIdx.x == 0) {
-                sc<T> tot = wacc0[0];
-                for (int w = 1; w < kWarps; ++w) tot = sc_add(tot, wacc0[w]);
-                S0 = tot;
-            }
-            __syncthreads();
-            double p1x = 0, p1y = 0, p2x = 0, p2y = 0;
-            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-                sc<T> se = acc[e];
-                for (int w = 1; w < kWarps; ++w) se = sc_add(se, acc[w * chunk + e]);
-                const sc<T> s0 = S0;
-                double Rx = 0, Ry = 0;
-                if (!sc_zero(se)) {
-                    const double f = ldexp(1.0, se.e - s0.e);
-                    const double ax = (double)se.x, ay = (double)se.y, bx = (double)s0.x, by = (double)s0.y;
-                    const double den = bx * bx + by * by;
-                    Rx = (ax * bx + ay * by) / den * f;
-                    Ry = (ay * bx - ax * by) / den * f;
-                }
-                const double c1 = (double)ent[e].c1, c2 = (double)ent[e].c2;
-                p1x += c1 * Rx; p1y += c1 * Ry;
-                p2x += c2 * Rx; p2y += c2 * Ry;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                p1x += __shfl_xor_sync(0xffffffffu, p1x, o);
-                p1y += __shfl_xor_sync(0xffffffffu, p1y, o);
-                p2x += __shfl_xor_sync(0xffffffffu, p2x, o);
-                p2y += __shfl_xor_sync(0xffffffffu, p2y, o);
-            }
-            if (lane == 0) { red[warp][0] = p1x; red[warp][1] = p1y; red[warp][2] = p2x; red[warp][3] = p2y; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (first_chunk) { Hs[0] = Hs[1] = Hs[2] = Hs[3] = 0.0; }
-                for (int w = 0; w < kWarps; ++w)
-                    for (int c = 0; c < 4; ++c) Hs[c] += red[w][c];
-            }
-            first_chunk = false;
-            __syncthreads();
-            if (cursor >= ncand) break;
         }
-        if (threadIdx.x == 0) {
-            const sc<T> s0 = S0;
-            const double diag = (double)diag_sh;
-            const double h1x = diag + Hs[0], h1y = Hs[1];
-            if (!sc_finite(s0) || sc_zero(s0) || !isfinite(h1x) || !isfinite(h1y)) flag_range(md.status);
-            if (h1_out) { h1_out[2 * smp] = h1x; h1_out[2 * smp + 1] = h1y; }
-            if (mode == 1 && h2_out) {
-                h2_out[2 * smp] = diag * h1x + Hs[2] + (double)cst_sh;
-                h2_out[2 * smp + 1] = diag * h1y + Hs[3];
+        if (first_chunk) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const sc<T> w{shfl_x(a0.x, o), shfl_x(a0.y, o), __shfl_xor_sync(0xffffffffu, a0.e, o)};
+                a0 = sc_add(a0, w);
             }
+            if (lane == 0) S.wacc0[warp] = a0;
         }
         __syncthreads();
+        if (first_chunk && threadIdx.x == 0) {
+            sc<T> tot = S.wacc0[0];
+            for (int w = 1; w < kWarps; ++w) tot = sc_add(tot, S.wacc0[w]);
+            S.S0 = tot;
+        }
+        __syncthreads();
+        double p1x = 0, p1y = 0, p2x = 0, p2y = 0;
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            sc<T> se = acc[e];
+            for (int w = 1; w < kWarps; ++w) se = sc_add(se, acc[w * chunk + e]);
+            const sc<T> s0 = S.S0;
+            double Rx = 0, Ry = 0;
+            if (!sc_zero(se)) {
+                const double f = ldexp(1.0, se.e - s0.e);
+                const double ax = (double)se.x, ay = (double)se.y, bx = (double)s0.x, by = (double)s0.y;
+                const double den = bx * bx + by * by;
+                Rx = (ax * bx + ay * by) / den * f;
+                Ry = (ay * bx - ax * by) / den * f;
+            }
+            const double c1 = (double)ent[e].c1, c2 = (double)ent[e].c2;
+            p1x += c1 * Rx; p1y += c1 * Ry;
+            p2x += c2 * Rx; p2y += c2 * Ry;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            p1x += __shfl_xor_sync(0xffffffffu, p1x, o);
+            p1y += __shfl_xor_sync(0xffffffffu, p1y, o);
+            p2x += __shfl_xor_sync(0xffffffffu, p2x, o);
+            p2y += __shfl_xor_sync(0xffffffffu, p2y, o);
+        }
+        if (lane == 0) { S.red[warp][0] = p1x; S.red[warp][1] = p1y; S.red[warp][2] = p2x; S.red[warp][3] = p2y; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (first_chunk) { S.Hs[0] = S.Hs[1] = S.Hs[2] = S.Hs[3] = 0.0; }
+            for (int w = 0; w < kWarps; ++w)
+                for (int c = 0; c < 4; ++c) S.Hs[c] += S.red[w][c];
+        }
+        first_chunk = false;
+        __syncthreads();
+        if (S.cursor >= ncand) break;
     }
+    if (threadIdx.x == 0) {
+        const sc<T> s0 = S.S0;
+        const double diag = (double)S.diag_sh;
+        const double h1x = diag + S.Hs[0], h1y = S.Hs[1];
+        if (!sc_finite(s0) || sc_zero(s0) || !isfinite(h1x) || !isfinite(h1y)) flag_range(md.status);
+        if (h1o) { h1o[0] = h1x; h1o[1] = h1y; }
+        if (mode == 1 && h2o) {
+            h2o[0] = diag * h1x + S.Hs[2] + (double)S.cst_sh;
+            h2o[1] = diag * h1y + S.Hs[3];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int GL, int MPL, int MODE>
+__global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
+                                                   int chunk, double *__restrict__ h1_out, double *__restrict__ h2_out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ EShared<T> S;
+    for (int64_t smp = blockIdx.x; smp < n; smp += gridDim.x)
+        eloc_sample<T, GL, MPL, MODE>(md, cfg + smp * md.nwords, chunk, h1_out ? h1_out + 2 * smp : nullptr,
+                                      h2_out ? h2_out + 2 * smp : nullptr, S, smem_raw);
 }
 
 // Launcher of one (T, GL, MPL) variant; each variant is instantiated in its

@@ -1,0 +1,6 @@
+// Mixed-batch body of tile shape GL = 16, MPL = 7 (relocatable device code).
+#include "k_mixed.cuh"
+
+namespace nnqs {
+NNQS_MIXED_DEF(16, 7)
+}  // namespace nnqs

@@ -1,0 +1,6 @@
+// Mixed-batch body of tile shape GL = 32, MPL = 4 (relocatable device code).
+#include "k_mixed.cuh"
+
+namespace nnqs {
+NNQS_MIXED_DEF(32, 4)
+}  // namespace nnqs

@@ -1,0 +1,6 @@
+// Mixed-batch body of tile shape GL = 8, MPL = 5 (relocatable device code).
+#include "k_mixed.cuh"
+
+namespace nnqs {
+NNQS_MIXED_DEF(8, 5)
+}  // namespace nnqs

@@ -67,18 +67,7 @@ __global__ void __launch_bounds__(32) k_moments_final(const double *__restrict__
         moments[0] = 1.0; moments[1] = m1; moments[2] = m2; moments[3] = m3;
         moments[4] = v[0]; moments[5] = v[4] / z; moments[6] = v[5] / z; moments[7] = 0.0;
     }
-    if (lanczos) {
-        // lowest eigenpair of the 2x2 matrix of H in span{psi0, psi1}
-        const double v2 = m2 - m1 * m1;
-        if (v2 <= 1e-14 * m1 * m1 || v2 <= 0.0) {
-            lanczos[0] = m1; lanczos[1] = v2 > 0.0 ? sqrt(v2) : 0.0; lanczos[2] = 0.0;
-        } else {
-            const double vv = sqrt(v2);
-            const double d = (m3 - 3.0 * m1 * m2 + 2.0 * m1 * m1 * m1) / (2.0 * v2 * vv);
-            const double al = d - sqrt(d * d + 1.0);
-            lanczos[0] = m1 + vv * al; lanczos[1] = vv; lanczos[2] = al;
-        }
-    }
+    if (lanczos) lanczos_p1(m1, m2, m3, lanczos);
 }
 
 cudaError_t launch_moments(const double *h1, const double *h2, int64_t n, double *partial, int nblocks,
@@ -164,12 +153,11 @@ template <typename T> __device__ __forceinline__ sc<T> exp_scaled(double x, doub
 }
 
 template <typename T>
-__global__ void k_tables_conn(const double *__restrict__ par, int N, int M, int K, int nb, int use_bias,
+__global__ void k_tables_conn(const double *__restrict__ par, int N, int M, int Mp, int K, int nb, int use_bias,
                               const int16_t *__restrict__ bi, const int16_t *__restrict__ bj, cx<T> *Tb, cx<T> *Cb,
                               cx<T> *S4, cx<T> *CS, sc<T> *ES)
 {
     const int64_t P1 = 1 + N + M + (int64_t)M * N;
-    const int Mp = conn_mpad(M);
     const int64_t n1 = (int64_t)K * nb * Mp, n2 = (int64_t)K * N * Mp, n3 = (int64_t)K * nb, n4 = (int64_t)K * N;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n1 + n2 + n3 + n4;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -242,16 +230,16 @@ __global__ void k_tables_conn(const double *__restrict__ par, int N, int M, int 
 }
 
 template <typename T>
-cudaError_t launch_tables_conn(const double *params, int N, int M, int K, int nb, int use_bias, const int16_t *bi,
-                               const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, sc<T> *ES,
-                               cudaStream_t st)
+cudaError_t launch_tables_conn(const double *params, int N, int M, int Mp, int K, int nb, int use_bias,
+                               const int16_t *bi, const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS,
+                               sc<T> *ES, cudaStream_t st)
 {
-    k_tables_conn<T><<<2048, 256, 0, st>>>(params, N, M, K, nb, use_bias, bi, bj, Tb, Cb, S4, CS, ES);
+    k_tables_conn<T><<<2048, 256, 0, st>>>(params, N, M, Mp, K, nb, use_bias, bi, bj, Tb, Cb, S4, CS, ES);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_tables_conn<float>(const double *, int, int, int, int, int, const int16_t *, const int16_t *, cx<float> *, cx<float> *, cx<float> *, cx<float> *, sc<float> *, cudaStream_t);
-template cudaError_t launch_tables_conn<double>(const double *, int, int, int, int, int, const int16_t *, const int16_t *, cx<double> *, cx<double> *, cx<double> *, cx<double> *, sc<double> *, cudaStream_t);
+template cudaError_t launch_tables_conn<float>(const double *, int, int, int, int, int, int, const int16_t *, const int16_t *, cx<float> *, cx<float> *, cx<float> *, cx<float> *, sc<float> *, cudaStream_t);
+template cudaError_t launch_tables_conn<double>(const double *, int, int, int, int, int, int, const int16_t *, const int16_t *, cx<double> *, cx<double> *, cx<double> *, cx<double> *, sc<double> *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_build_tables(const double *params, int N, int M, int K, cx<T> *Wt, cx<T> *b, cx<T> *a, cx<T> *logc,

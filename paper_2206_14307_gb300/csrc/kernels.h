@@ -21,6 +21,26 @@ template <typename T>
 cudaError_t launch_ratio(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int mode, double *h1, double *h2,
                          int nsm, cudaStream_t st);
 
+// one tile variant (see variant_width) of the connected-configuration engine
+template <typename T>
+cudaError_t launch_ratio_variant(const DevModel<T> &md, int v, const uint64_t *cfg, int64_t n, int mode, double *h1,
+                                 double *h2, int nsm, cudaStream_t st);
+
+// Mixed batch (Lanczos mode): one persistent launch over (instance, sample)
+// items; each instance runs with its own tile shape (GL lanes per row, MPL
+// hidden units per lane).
+constexpr int kNumTileShapes = 16;
+constexpr int kTileGL[kNumTileShapes] = {8, 8, 16, 8, 8, 16, 8, 16, 16, 16, 32, 16, 32, 32, 32, 32};
+constexpr int kTileMPL[kNumTileShapes] = {2, 4, 2, 5, 8, 4, 9, 5, 7, 8, 4, 9, 7, 8, 13, 16};
+struct BatchItem { int model, sample, out; };
+// sets the kernel's shared-memory limit; returns the number of resident CTAs (0 on error)
+int mixed_grid(int nsm);
+cudaError_t launch_mixed(int grid, const DevModel<float> *models, const int *shape, const BatchItem *items,
+                         int nitems, int *counter, const uint64_t *cfg_all, const int64_t *cfg_off, double *h1_all,
+                         double *h2_all, cudaStream_t st);
+cudaError_t launch_moments_batched(const double *h1_all, const double *h2_all, const int64_t *out_off, int nmodels,
+                                   double *moments, double *lanczos, cudaStream_t st);
+
 // Bytes of per-chain cache the sampler needs, and the number of chains that
 // run concurrently (the cache is needed for those only).
 template <typename T> size_t sampler_cache_bytes(const DevModel<T> &md);
@@ -59,9 +79,9 @@ cudaError_t launch_build_tables(const double *params, int N, int M, int K, cx<T>
                                 cx2<T> *X, cx2<T> *XA, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_tables_conn(const double *params, int N, int M, int K, int nb, int use_bias, const int16_t *bi,
-                               const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS, sc<T> *ES,
-                               cudaStream_t st);
+cudaError_t launch_tables_conn(const double *params, int N, int M, int Mp, int K, int nb, int use_bias,
+                               const int16_t *bi, const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS,
+                               sc<T> *ES, cudaStream_t st);
 
 // tensor-core (tcgen05) log psi with BF16-split weights: NS = 2 or 3 terms
 bool tc_supported(int N, int M, int G, int K, int nsign, int NS);

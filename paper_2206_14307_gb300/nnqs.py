@@ -28,6 +28,9 @@ ABI_FUNCTIONS = (
     "nnqs_set_params_device", "nnqs_sample", "nnqs_log_psi", "nnqs_local_energy",
     "nnqs_lanczos_moments", "nnqs_grad_logpsi", "nnqs_energy_grad", "nnqs_sr_matvec",
     "nnqs_status", "nnqs_last_error", "nnqs_lanczos_moments_noalloc", "nnqs_sr_solve",
+    "nnqs_num_tile_shapes", "nnqs_tile_shape", "nnqs_batch_create", "nnqs_batch_destroy", "nnqs_batch_size",
+    "nnqs_batch_model", "nnqs_batch_get_shape", "nnqs_batch_set_shape", "nnqs_batch_autotune",
+    "nnqs_batch_lanczos", "nnqs_batch_status",
 )
 NOALLOC_MAX_SAMPLES = 65536
 
@@ -77,6 +80,17 @@ def lib():
             "nnqs_status": ([P, P], ctypes.c_int),
             "nnqs_lanczos_moments_noalloc": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_last_error": ([], ctypes.c_char_p),
+            "nnqs_num_tile_shapes": ([], i32),
+            "nnqs_tile_shape": ([i32, P, P], ctypes.c_int),
+            "nnqs_batch_create": ([P, i32, ctypes.POINTER(P)], ctypes.c_int),
+            "nnqs_batch_destroy": ([P], ctypes.c_int),
+            "nnqs_batch_size": ([P], i32),
+            "nnqs_batch_model": ([P, i32], P),
+            "nnqs_batch_get_shape": ([P, i32], i32),
+            "nnqs_batch_set_shape": ([P, i32, i32], ctypes.c_int),
+            "nnqs_batch_autotune": ([P, P, P, i32, P, P, P], ctypes.c_int),
+            "nnqs_batch_lanczos": ([P, P, P, P, P, P, P, P], ctypes.c_int),
+            "nnqs_batch_status": ([P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -135,6 +149,48 @@ def nnqs_status(h, stream=0): return _check(lib().nnqs_status(h, stream))
 
 def nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream=0):
     return _check(lib().nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream))
+
+
+def nnqs_num_tile_shapes(): return lib().nnqs_num_tile_shapes()
+
+
+def nnqs_tile_shape(v):
+    gl, mpl = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().nnqs_tile_shape(v, ctypes.byref(gl), ctypes.byref(mpl)))
+    return gl.value, mpl.value
+
+
+def nnqs_batch_create(descs) -> int:
+    arr = (nnqs_desc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _check(lib().nnqs_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(descs), ctypes.byref(h)))
+    return h.value
+
+
+def nnqs_batch_destroy(b): return _check(lib().nnqs_batch_destroy(b))
+def nnqs_batch_size(b): return lib().nnqs_batch_size(b)
+
+
+def nnqs_batch_model(b, i):
+    h = lib().nnqs_batch_model(b, i)
+    if not h:
+        raise NNQSError(NNQS_EINVAL, lib().nnqs_last_error().decode())
+    return h
+
+
+def nnqs_batch_get_shape(b, i): return lib().nnqs_batch_get_shape(b, i)
+def nnqs_batch_set_shape(b, i, v): return _check(lib().nnqs_batch_set_shape(b, i, v))
+
+
+def nnqs_batch_autotune(b, cfg, n_per_model_host, probe, shape_out_host, ms_out_host, stream=0):
+    return _check(lib().nnqs_batch_autotune(b, cfg, n_per_model_host, probe, shape_out_host, ms_out_host, stream))
+
+
+def nnqs_batch_lanczos(b, cfg, n_per_model_host, h1, h2, moments, lanczos, stream=0):
+    return _check(lib().nnqs_batch_lanczos(b, cfg, n_per_model_host, h1, h2, moments, lanczos, stream))
+
+
+def nnqs_batch_status(b, stream=0): return _check(lib().nnqs_batch_status(b, stream))
 
 
 # ---- torch convenience wrapper ---------------------------------------------------------------
@@ -257,3 +313,86 @@ def cfg_tensor(words: np.ndarray):
     """uint64 numpy words -> int64 CUDA tensor with the same bits."""
     import torch
     return torch.from_numpy(np.ascontiguousarray(words).view(np.int64)).cuda()
+
+
+class _Borrowed(Model):
+    """Model view of a batch instance (owned by the batch)."""
+
+    def __init__(self, h, desc):
+        self.h = h
+        self.desc = desc
+        self.L, self.N, self.M, self.K = desc.L, desc.L * desc.L, desc.M, desc.K
+        self.P = nnqs_num_params(h)
+        self.G = nnqs_group_size(h)
+        self.nwords = (self.N + 63) // 64
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Instances of uneven size run in one persistent, graph-captured launch.
+    ``specs`` are dicts of Model's keyword arguments (L, J1, J2, K, M, proj_t,
+    proj_p, momentum, irrep, spin_inv, use_bias, precision)."""
+
+    def __init__(self, specs):
+        descs = []
+        for sp in specs:
+            L = sp["L"]
+            M = sp.get("M") or L * L
+            descs.append(nnqs_desc(L, sp.get("J1", 1.0), sp.get("J2", 0.5), sp.get("K", 1), M,
+                                   int(sp.get("proj_t", False)), int(sp.get("proj_p", False)),
+                                   sp.get("momentum", K00), sp.get("irrep", A1), sp.get("spin_inv", 0),
+                                   int(sp.get("use_bias", True)), sp.get("precision", FP32)))
+        self.h = nnqs_batch_create(descs)
+        self.models = [_Borrowed(nnqs_batch_model(self.h, i), d) for i, d in enumerate(descs)]
+
+    def __len__(self):
+        return len(self.models)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.models:
+                m.h = None
+            nnqs_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _counts(counts):
+        return np.ascontiguousarray(np.asarray(counts, np.int64))
+
+    def shape(self, i):
+        return nnqs_batch_get_shape(self.h, i)
+
+    def set_shape(self, i, v):
+        nnqs_batch_set_shape(self.h, i, v)
+
+    def autotune(self, cfg, counts, probe=64):
+        """cfg: int64 CUDA tensor holding every instance's words back to back."""
+        n = self._counts(counts)
+        shapes = np.zeros(len(self), np.int32)
+        ms = np.zeros(len(self), np.float64)
+        nnqs_batch_autotune(self.h, cfg.data_ptr(), n.ctypes.data, probe, shapes.ctypes.data, ms.ctypes.data,
+                            _stream())
+        return shapes, ms
+
+    def lanczos(self, cfg, counts, h1=None, h2=None, moments=None, lanczos=None):
+        import torch
+        n = self._counts(counts)
+        tot = int(n.sum())
+        h1 = torch.empty(tot, 2, dtype=torch.float64, device="cuda") if h1 is None else h1
+        h2 = torch.empty(tot, 2, dtype=torch.float64, device="cuda") if h2 is None else h2
+        moments = torch.empty(len(self), 8, dtype=torch.float64, device="cuda") if moments is None else moments
+        lanczos = torch.empty(len(self), 3, dtype=torch.float64, device="cuda") if lanczos is None else lanczos
+        nnqs_batch_lanczos(self.h, cfg.data_ptr() if tot else None, n.ctypes.data, h1.data_ptr(), h2.data_ptr(),
+                           moments.data_ptr(), lanczos.data_ptr(), _stream())
+        return h1, h2, moments, lanczos
+
+    def status(self):
+        return nnqs_batch_status(self.h, _stream())

@@ -8,6 +8,9 @@ Sec. 3.4): complex RBM parameters with independent N(0, std^2) real and
 imaginary parts (std 0.01 by default, 0.05 for the "stress" variant), drawn
 from numpy's PCG64 stream of the given seed; configurations uniform over the
 Sz = 0 sector (a random permutation of N/2 up and N/2 down spins per row).
+Mixed batches of instances draw (L, J2, alpha, K) from numpy's Philox stream
+of the given seed: L in {4, 6, 8, 10}, J2/J1 uniform in [0, 0.7], alpha in
+{1, 2, 4} (M = alpha N), K in {1, 2}.
 """
 from __future__ import annotations
 
@@ -66,4 +69,17 @@ def unpack(words_: np.ndarray, N: int) -> np.ndarray:
     out = np.empty((w.shape[0], N), np.int8)
     for i in range(N):
         out[:, i] = np.where((w[:, i // 64] >> np.uint64(i % 64)) & np.uint64(1), 1, -1)
+    return out
+
+
+def mixed_batch(n: int = 64, seed: int = 5) -> list[dict]:
+    """n instance shapes of a mixed batch: dicts with L, J2, alpha, K, M."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for _ in range(n):
+        L = int(rng.choice([4, 6, 8, 10]))
+        J2 = float(rng.uniform(0.0, 0.7))
+        alpha = int(rng.choice([1, 2, 4]))
+        K = int(rng.choice([1, 2]))
+        out.append(dict(L=L, J2=J2, alpha=alpha, K=K, M=alpha * L * L))
     return out

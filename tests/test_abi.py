@@ -67,3 +67,35 @@ def test_odd_inversion_without_bias_rejected(lib):
 def test_null_model_is_einval(lib):
     assert lib.nnqs_log_psi(None, None, 1, None, None) == -1
     assert lib.nnqs_num_params(None) == -1
+
+
+def test_tile_shape_table(lib):
+    from paper_2206_14307_gb300 import nnqs
+    n = lib.nnqs_num_tile_shapes()
+    assert n == 16
+    widths = []
+    for v in range(n):
+        gl, mpl = nnqs.nnqs_tile_shape(v)
+        assert gl in (8, 16, 32) and 1 <= mpl <= 16
+        widths.append(gl * mpl)
+    assert widths == sorted(widths) and widths[0] == 16 and widths[-1] == 512
+    with pytest.raises(nnqs.NNQSError):
+        nnqs.nnqs_tile_shape(n)
+
+
+def test_batch_arguments_rejected_on_host(lib):
+    from paper_2206_14307_gb300 import nnqs
+    ok = nnqs.nnqs_desc(4, 1.0, 0.5, 1, 16, 0, 0, 0, 0, 0, 1, nnqs.FP32)
+    f64 = nnqs.nnqs_desc(4, 1.0, 0.5, 1, 16, 0, 0, 0, 0, 0, 1, nnqs.FP64)
+    arr = (nnqs.nnqs_desc * 2)(ok, f64)
+    h = ctypes.c_void_p()
+    assert lib.nnqs_batch_create(ctypes.cast(arr, ctypes.c_void_p), 2, ctypes.byref(h)) == nnqs.NNQS_EUNSUPPORTED
+    assert h.value is None
+    assert lib.nnqs_batch_create(ctypes.cast(arr, ctypes.c_void_p), 0, ctypes.byref(h)) == nnqs.NNQS_EINVAL
+    assert lib.nnqs_batch_create(None, 1, ctypes.byref(h)) == nnqs.NNQS_EINVAL
+    assert lib.nnqs_batch_size(None) == -1
+    assert lib.nnqs_batch_get_shape(None, 0) == -1
+    assert lib.nnqs_batch_model(None, 0) is None
+    assert lib.nnqs_batch_lanczos(None, None, None, None, None, None, None, None) == nnqs.NNQS_EINVAL
+    assert lib.nnqs_batch_autotune(None, None, None, 1, None, None, None) == nnqs.NNQS_EINVAL
+    assert lib.nnqs_batch_destroy(None) == nnqs.NNQS_OK

@@ -90,3 +90,15 @@ def test_rank_select_and_init():
         cnt[ups.index(iu)] += 1
     chi2 = ((cnt - 1000) ** 2 / 1000).sum()
     assert chi2 < 30   # 7 dof; p ~ 1e-4
+
+
+def test_mixed_batch_instances_are_seeded_and_in_range():
+    from paper_2206_14307_gb300 import synth
+    a = synth.mixed_batch(64, seed=5)
+    assert a == synth.mixed_batch(64, seed=5)
+    assert a != synth.mixed_batch(64, seed=6)
+    assert len(a) == 64
+    for d in a:
+        assert d["L"] in (4, 6, 8, 10) and d["alpha"] in (1, 2, 4) and d["K"] in (1, 2)
+        assert 0.0 <= d["J2"] <= 0.7 and d["M"] == d["alpha"] * d["L"] ** 2
+    assert {d["L"] for d in a} == {4, 6, 8, 10}
