@@ -19,6 +19,15 @@ psi(s') over all K|G| x 2 x M hidden terms: sampler proposals + fresh
 amplitudes + connected configurations of E_loc), and E_loc samples/s; the same
 step in the plain FP64 GPU form is timed beside it.
 
+Beside it (the metric's second half), one p = 1 Lanczos step on the 8x8
+configuration: L = 8, M = 128, |G| = 512, no inversion, 4096 sampler-drawn
+samples; nnqs_lanczos_moments gives h1 = (H psi)/psi, h2 = (H^2 psi)/psi, the
+FP64 moments <H^n> (n <= 3) and E_p1.  Lanczos E_loc samples/s is timed on
+the full set in the FP32 engine, and on a common 512-sample subset in both
+the FP32 and the plain FP64 GPU forms for the speedup.  `--mixed` adds the
+64-instance mixed batch (one persistent graph-captured launch; about 80 s a
+call, so not in the default run).
+
 Timing: CUDA events on the launching stream, per step, with a 512 MB L2 flush
 before every timed step (outside the events); W warm-up steps; barrier and the
 maximum over ranks.  `e2e` repeats the step through the public API with the
@@ -55,6 +64,10 @@ FLOPS_PER_ELEMENT = 28   # one connected factor p e^D + (1-p) e^-D and its runni
 K_RATIO_TRAFFIC = 8 * 0.418304e6
 
 
+LZ_L, LZ_M, LZ_SAMPLES, LZ_SUBSET = 8, 128, 4096, 512
+LZ_WORKLOAD = "8x8 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=128), 512 ops; 4096 samples; one Lanczos step"
+
+
 def bonds(L):
     dx, dy = (1, 0, 1, 1), (0, 1, 1, -1)
     out = []
@@ -70,6 +83,43 @@ def n_antialigned(words):
     s = synth.unpack(words, N)
     b = bonds(L)
     return int((s[:, b[:, 0]] != s[:, b[:, 1]]).sum())
+
+
+def rank_seed(rank, k):
+    """Sampler seed of step k on a rank: ranks draw disjoint Philox streams, so
+    N ranks run N times the chains (weak scaling, no collective on the data
+    path)."""
+    return 14307 + 1000003 * rank + k
+
+
+def max_over_ranks(vals, device="cuda"):
+    """Per-rank timings -> their maximum over ranks (the job's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def lanczos_entries(spins, L):
+    """Flip sets the Lanczos step evaluates per configuration (Sec. 3.3): every
+    anti-aligned bond b1 (first level) and, after exchanging b1, every bond b2
+    anti-aligned in the new configuration -- disjoint pairs once, pairs sharing
+    a site as the flipped site pair.  A bond sharing one site with b1 is
+    anti-aligned after the exchange iff it was aligned before."""
+    b = bonds(L)
+    nb = len(b)
+    share = ((b[:, None, 0] == b[None, :, 0]) | (b[:, None, 0] == b[None, :, 1]) |
+             (b[:, None, 1] == b[None, :, 0]) | (b[:, None, 1] == b[None, :, 1])).astype(np.int64)
+    np.fill_diagonal(share, 0)
+    disjoint = 1 - share
+    np.fill_diagonal(disjoint, 0)
+    aa = (spins[:, b[:, 0]] != spins[:, b[:, 1]]).astype(np.int64)
+    n_aa = aa.sum(1)
+    pairs = ((aa @ disjoint) * aa).sum(1) // 2
+    site = ((aa @ share) * (1 - aa)).sum(1)
+    return n_aa + pairs + site
 
 
 class ClockSampler:
@@ -142,7 +192,7 @@ def gpu_arm(args, rank, world):
     st = torch.cuda.current_stream()
 
     def step(model, k, e2e=False):
-        seed = 14307 + 1000003 * rank + k
+        seed = rank_seed(rank, k)
         if e2e:
             params_dev.copy_(params_pinned, non_blocking=True)
             model.set_params(params_dev.view(-1, 2))
@@ -164,7 +214,7 @@ def gpu_arm(args, rank, world):
             torch.cuda.synchronize()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             ev[0].record(st)
-            seed = 14307 + 1000003 * rank + warmup + k
+            seed = rank_seed(rank, warmup + k)
             if e2e:
                 params_dev.copy_(params_pinned, non_blocking=True)
                 model.set_params(params_dev.view(-1, 2))
@@ -206,7 +256,104 @@ def gpu_arm(args, rank, world):
         res.update(ms64=ms64, ms64_eloc=ms64_eloc, ms64_logpsi=ms64_logpsi)
         m64.close()
     m32.close()
+    if not args.no_lanczos:
+        res["lanczos"] = lanczos_leg(args, rank, flush)
+    if args.mixed:
+        res["mixed"] = mixed_leg(flush)
     return res
+
+
+def _event_ms(fn, flush, reps):
+    import torch
+    st = torch.cuda.current_stream()
+    best = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        best.append(e0.elapsed_time(e1))
+    return float(np.mean(best))
+
+
+def lanczos_leg(args, rank, flush):
+    """One p = 1 Lanczos step of the 8x8 configuration (FP32 engine; FP64 form
+    on a common subset)."""
+    import torch
+    from paper_2206_14307_gb300 import nnqs, synth
+    Ll, Nl, Ml = LZ_L, LZ_L * LZ_L, LZ_M
+    p = synth.random_params(Nl, Ml, 1, std=PARAM_STD, seed=PARAM_SEED)
+
+    def make(prec):
+        m = nnqs.Model(Ll, J1, J2, K=1, M=Ml, proj_t=True, proj_p=True, spin_inv=0, use_bias=True, precision=prec)
+        m.set_params(p)
+        return m
+
+    m32 = make(nnqs.FP32)
+    cfg, _ = m32.sample(rank_seed(rank, 0), 256, LZ_SAMPLES // 256, N_SKIP, 10 * N_SKIP)
+    sub = cfg[:LZ_SUBSET].contiguous()
+    h1 = torch.empty(LZ_SAMPLES, 2, dtype=torch.float64, device="cuda")
+    h2 = torch.empty_like(h1)
+    mo = torch.empty(8, dtype=torch.float64, device="cuda")
+    lz = torch.empty(3, dtype=torch.float64, device="cuda")
+    full = lambda: m32.lanczos(cfg, h1, h2, mo, lz)
+    full()
+    ms_full = _event_ms(full, flush, max(1, args.lanczos_steps))
+    e_p1 = float(lz[0].item()) / Nl
+    m1 = float(mo[1].item()) / Nl
+    m32.status()
+    small = lambda m: (lambda: m.lanczos(sub, h1[:LZ_SUBSET], h2[:LZ_SUBSET], mo, lz))
+    small(m32)()
+    ms_sub32 = _event_ms(small(m32), flush, 1)
+    spins = synth.unpack(cfg.cpu().numpy().view(np.uint64), Nl)
+    ent = lanczos_entries(spins, Ll)
+    G = m32.G
+    out = dict(ms=ms_full, samples=LZ_SAMPLES, entries=int(ent.sum()), G=G, e_p1=e_p1, m1=m1,
+               ms_sub32=ms_sub32, sub_entries=int(ent[:LZ_SUBSET].sum()))
+    m32.close()
+    if not args.no_fp64:
+        m64 = make(nnqs.FP64)
+        small(m64)()
+        out["ms_sub64"] = _event_ms(small(m64), flush, 1)
+        m64.close()
+    return out
+
+
+def mixed_leg(flush):
+    """The 64-instance mixed batch: L in {4,6,8,10}, J2/J1 in [0,0.7],
+    alpha in {1,2,4}, K in {1,2}, full projection, 256 samples each; autotuned
+    tile shapes; one graph replay = one Lanczos step of every instance."""
+    import torch
+    from paper_2206_14307_gb300 import nnqs, synth
+    inst = synth.mixed_batch(64, seed=5)
+    specs = [dict(L=d["L"], M=d["M"], K=d["K"], J2=d["J2"], proj_t=True, proj_p=True, spin_inv=0,
+                  use_bias=True, precision=nnqs.FP32) for d in inst]
+    counts = [256] * len(inst)
+    b = nnqs.Batch(specs)
+    cfgs = []
+    for i, d in enumerate(inst):
+        b.models[i].set_params(synth.random_params(d["L"] ** 2, d["M"], d["K"], std=PARAM_STD, seed=5000 + i))
+        c, _ = b.models[i].sample(14307 + i, 16, 16, N_SKIP, 10 * N_SKIP)
+        cfgs.append(c.reshape(-1))
+    cfg = torch.cat(cfgs)
+    tot = sum(counts)
+    h1 = torch.empty(tot, 2, dtype=torch.float64, device="cuda")
+    h2 = torch.empty_like(h1)
+    mo = torch.empty(len(inst), 8, dtype=torch.float64, device="cuda")
+    lz = torch.empty(len(inst), 3, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    shapes, _ = b.autotune(cfg, counts, probe=64)
+    t_tune = time.perf_counter() - t0
+    run = lambda: b.lanczos(cfg, counts, h1, h2, mo, lz)
+    run()
+    ms = _event_ms(run, flush, 1)
+    b.status()
+    b.close()
+    return dict(ms=ms, samples=tot, instances=len(inst), autotune_s=t_tune,
+                shapes=[int(x) for x in shapes])
 
 
 def cpu_baseline(budget_s=20.0):
@@ -269,6 +416,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-lanczos", action="store_true", help="skip the 8x8 Lanczos leg")
+    ap.add_argument("--lanczos-steps", type=int, default=2)
+    ap.add_argument("--mixed", action="store_true", help="add the 64-instance mixed batch (about 80 s)")
     ap.add_argument("--small", action="store_true",
                     help="128 chains instead of 1024 (for profiler captures; not a bench line)")
     args = ap.parse_args()
@@ -296,12 +446,8 @@ def main():
         dist.barrier()
     res = gpu_arm(args, rank, world)
     ms, e2e_ms = res["ms"], res["e2e_ms"]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e_ms, res.get("ms64", 0.0)], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms, ms64 = t.tolist()
+    ms, e2e_ms, ms64 = max_over_ranks([ms, e2e_ms, res.get("ms64", 0.0)])
+    if "ms64" in res:
         res["ms64"] = ms64
     if rank != 0:
         return
@@ -341,6 +487,33 @@ def main():
                             "ms_per_step": res["ms64"], "steps": args.fp64_steps, "warmup": 1,
                             "fresh_amplitudes_per_s": N_SAMPLES / (res["ms64_logpsi"] / 1e3)}
         line["speedup_vs_fp64_gpu"] = res["ms64"] / ms
+    if "lanczos" in res:
+        lz = res["lanczos"]
+        Ml = LZ_M
+        lz_elems = lz["entries"] * lz["G"] * Ml
+        lz_ach = lz_elems * FLOPS_PER_ELEMENT / (lz["ms"] / 1e3) / 1e12
+        line["lanczos"] = {
+            "workload": LZ_WORKLOAD, "metric": "Lanczos E_loc samples/s (h1 and h2 at one sample)",
+            "value": world * lz["samples"] / (lz["ms"] / 1e3), "unit": "samples/s", "ms_per_step": lz["ms"],
+            "steps": args.lanczos_steps, "warmup": 1, "dtype": "f32 (FP64 moments)",
+            "E_p1_per_site": lz["e_p1"], "m1_per_site": lz["m1"],
+            "flip_sets_per_sample": lz["entries"] / lz["samples"],
+            "roofline": {"kernel": "k_eloc Lanczos mode (all flip-set kinds)", "bound": "alu",
+                         "achieved": lz_ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": lz_ach / FP32_PEAK_TFLOPS, "traffic": None,
+                         "work": f"{lz['entries']} flip sets x |G|={lz['G']} x M={Ml} x {FLOPS_PER_ELEMENT} flop"},
+        }
+        if "ms_sub64" in lz:
+            line["lanczos"]["fp64_gpu"] = {"value": LZ_SUBSET / (lz["ms_sub64"] / 1e3), "unit": "samples/s",
+                                           "subset": LZ_SUBSET}
+            line["lanczos"]["fp32_same_subset"] = LZ_SUBSET / (lz["ms_sub32"] / 1e3)
+            line["lanczos"]["speedup_vs_fp64_gpu"] = lz["ms_sub64"] / lz["ms_sub32"]
+    if "mixed" in res:
+        mx = res["mixed"]
+        line["mixed_batch"] = {"workload": "64 instances (Philox seed 5): L in {4,6,8,10}, J2/J1 in [0,0.7], "
+                                           "alpha in {1,2,4}, K in {1,2}, 8N ops; 256 samples each",
+                               "value": mx["samples"] / (mx["ms"] / 1e3), "unit": "Lanczos samples/s",
+                               "ms_per_step": mx["ms"], "autotune_s": mx["autotune_s"], "shapes": mx["shapes"]}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_baseline"].pop("eloc_samples_per_s", None)
