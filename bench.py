@@ -24,7 +24,8 @@ configuration: L = 8, M = 128, |G| = 512, no inversion, 4096 sampler-drawn
 samples; nnqs_lanczos_moments gives h1 = (H psi)/psi, h2 = (H^2 psi)/psi, the
 FP64 moments <H^n> (n <= 3) and E_p1.  Lanczos E_loc samples/s is timed on
 the full set in the FP32 engine, and on a common 512-sample subset in both
-the FP32 and the plain FP64 GPU forms for the speedup.  `--mixed` adds the
+the FP32 and the plain FP64 GPU forms for the speedup (912 = 6 x 152
+samples, whole waves of resident CTAs in both forms).  `--mixed` adds the
 64-instance mixed batch (one persistent graph-captured launch; about 80 s a
 call, so not in the default run).
 
@@ -64,7 +65,7 @@ FLOPS_PER_ELEMENT = 28   # one connected factor p e^D + (1-p) e^-D and its runni
 K_RATIO_TRAFFIC = 8 * 0.418304e6
 
 
-LZ_L, LZ_M, LZ_SAMPLES, LZ_SUBSET = 8, 128, 4096, 512
+LZ_L, LZ_M, LZ_SAMPLES, LZ_SUBSET = 8, 128, 4096, 912   # subset: 6 x 152 SMs
 LZ_WORKLOAD = "8x8 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=128), 512 ops; 4096 samples; one Lanczos step"
 
 

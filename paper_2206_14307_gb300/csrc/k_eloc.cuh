@@ -579,8 +579,18 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
     __syncthreads();
 }
 
+// CTAs per SM the register budget is sized for: three (80 registers) where
+// the FP32 variant needs no spill at that budget, else what the compiler picks.
+template <typename T, int GL, int MPL, int MODE> constexpr int eloc_min_blocks()
+{
+    if (sizeof(T) != 4) return 1;
+    if (GL == 8) return (MPL <= 4 || MODE == 0) ? 3 : 1;
+    if (GL == 16) return MPL == 8 ? 3 : 1;
+    return MPL == 8 ? 3 : 1;
+}
+
 template <typename T, int GL, int MPL, int MODE>
-__global__ void __launch_bounds__(kThreads) k_eloc(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
+__global__ void __launch_bounds__(kThreads, eloc_min_blocks<T, GL, MPL, MODE>()) k_eloc(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
                                                    int chunk, double *__restrict__ h1_out, double *__restrict__ h2_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -598,10 +608,18 @@ template <typename T, int GL> size_t eloc_smem(int chunk)
     return (sizeof(Entry2<T>) + kWarps * sizeof(sc<T>)) * (size_t)chunk + tiles;
 }
 
+// Entries gathered per pass in the Lanczos mode: small enough that the
+// shared memory of three CTAs fits an SM where the registers allow three.
+template <typename T, int GL, int MPL> constexpr int eloc_lanczos_chunk()
+{
+    return eloc_min_blocks<T, GL, MPL, 1>() < 3 ? 512 : (GL == 16 ? 160 : 384);
+}
+
 template <typename T, int GL, int MPL, int MODE>
 cudaError_t launch_eloc_mode(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int chunk, double *h1, double *h2,
                              int nsm, cudaStream_t st)
 {
+    if (MODE == 1) chunk = eloc_lanczos_chunk<T, GL, MPL>();
     const size_t smem = eloc_smem<T, GL>(chunk);
     cudaError_t err =
         cudaFuncSetAttribute(k_eloc<T, GL, MPL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
