@@ -57,6 +57,8 @@ def lib():
         L.or_lanczos_h.argtypes = [P, P, i, P, P]
         L.or_moments.argtypes = [i, P, P, P, P]
         L.or_lanczos_step.argtypes = [P, P]
+        L.or_lanczos_variance.argtypes = [P, P, P]
+        L.or_structure_factor.argtypes = [i, P, i, P, P]
         L.or_energy_grad.argtypes = [i, i, P, P, P, P]
         L.or_sr_solve.argtypes = [i, i, P, P, d, d, P]
         L.or_philox4x32_10.argtypes = [P, P, P]
@@ -190,10 +192,10 @@ def moments(h1, h2=None, weights=None):
         h2 = np.asarray(h2, np.complex128)
         b = np.ascontiguousarray(np.stack([h2.real, h2.imag], -1))
     w = None if weights is None else np.ascontiguousarray(np.asarray(weights, np.float64))
-    out = np.zeros(7)
+    out = np.zeros(8)
     lib().or_moments(n, _p(a), _p(b) if b is not None else None,
                      _p(w) if w is not None else None, _p(out))
-    return dict(m=out[:4].copy(), z=out[4], im_h1=out[5], im_h1h2=out[6])
+    return dict(m=out[:4].copy(), z=out[4], im_h1=out[5], im_h1h2=out[6], m4=out[7])
 
 
 def lanczos_step(m):
@@ -201,6 +203,26 @@ def lanczos_step(m):
     out = np.zeros(3)
     lib().or_lanczos_step(_p(m), _p(out))
     return dict(E=out[0], v=out[1], alpha=out[2])
+
+
+def lanczos_variance(m, lz):
+    """m: m0..m4; lz: {E, v, alpha} or [E, v, alpha] -> dict var0, E1, var1, E_extrap."""
+    mm = np.ascontiguousarray(np.asarray(m, np.float64)[:5])
+    if isinstance(lz, dict):
+        lz = [lz["E"], lz["v"], lz["alpha"]]
+    ll = np.ascontiguousarray(np.asarray(lz, np.float64))
+    out = np.zeros(4)
+    lib().or_lanczos_variance(_p(mm), _p(ll), _p(out))
+    return dict(var0=out[0], E1=out[1], var1=out[2], E_extrap=out[3])
+
+
+def structure_factor(L, spins, weights=None):
+    """S(q) for q = 2 pi (qx, qy)/L, array [L*L] indexed qx + L qy."""
+    s = np.ascontiguousarray(np.asarray(spins, np.int8).reshape(-1, L * L))
+    w = None if weights is None else np.ascontiguousarray(np.asarray(weights, np.float64))
+    out = np.zeros(L * L)
+    lib().or_structure_factor(L, _p(s), len(s), _p(w) if w is not None else None, _p(out))
+    return out
 
 
 def energy_grad(O, eloc, weights=None):

@@ -18,8 +18,11 @@
  *   - Local energy Eq. 10 by enumerating bonds and re-evaluating psi from
  *     scratch at every connected configuration (no incremental update).
  *   - (H^2 psi)/psi by explicit double enumeration (Sec. 3.3).
- *   - Moments <H^n>, n<=3, and the p=1 Lanczos energy, Eqs. 13-18, with the
- *     closed form re-derived from the 2x2 matrix in span{psi0, psi1}.
+ *   - Moments <H^n>, n<=4, and the p=1 Lanczos energy, Eqs. 13-18, with the
+ *     closed form re-derived from the 2x2 matrix in span{psi0, psi1}; the
+ *     p=1 state's variance and the variance extrapolation (Sec. 4.3).
+ *   - Static spin structure factor S(q) (Sec. 4.1) as the double sum over
+ *     site pairs.
  *   - Log-derivatives O_k and the SR system, Eq. 12.
  *   - Metropolis pair-exchange sampling, Sec. 3.2, driven by Philox4x32-10
  *     (Salmon, Moraes, Dror, Shaw, SC'11) written from its published
@@ -379,7 +382,7 @@ static double pairwise(const double *v, int n)
 
 void or_moments(int n, const double *h1, const double *h2, const double *weights, double *out)
 {
-    double *c = (double *)malloc(sizeof(double) * 6 * (size_t)n);
+    double *c = (double *)malloc(sizeof(double) * 7 * (size_t)n);
     for (int k = 0; k < n; ++k) {
         double w = weights ? weights[k] : 1.0;
         cplx a = h1[2 * k] + I * h1[2 * k + 1];
@@ -391,6 +394,7 @@ void or_moments(int n, const double *h1, const double *h2, const double *weights
         c[3 * (size_t)n + k] = w * creal(ab);
         c[4 * (size_t)n + k] = w * cimag(a);
         c[5 * (size_t)n + k] = w * cimag(ab);
+        c[6 * (size_t)n + k] = w * (creal(b) * creal(b) + cimag(b) * cimag(b));
     }
     double z = pairwise(c, n);
     out[0] = 1.0;
@@ -400,6 +404,7 @@ void or_moments(int n, const double *h1, const double *h2, const double *weights
     out[4] = z;
     out[5] = pairwise(c + 4 * (size_t)n, n) / z;
     out[6] = pairwise(c + 5 * (size_t)n, n) / z;
+    out[7] = pairwise(c + 6 * (size_t)n, n) / z;   /* m4 = <H^4> = <|h2|^2> */
     free(c);
 }
 
@@ -420,6 +425,67 @@ void or_lanczos_step(const double *m, double *out)
     double d = (m3 - 3 * m1 * m2 + 2 * m1 * m1 * m1) / (2 * v2 * v);
     double alpha = d - sqrt(d * d + 1);
     out[0] = m1 + v * alpha; out[1] = v; out[2] = alpha;
+}
+
+/* Energy and variance of the p = 1 Lanczos state, and the variance
+ * extrapolation (Sec. 3.3 Eq. 16; Sec. 4.3).  The state is phi = psi0 +
+ * alpha psi1 with psi1 = (H - m1) psi0 / v, i.e. phi = a psi0 + b H psi0 with
+ * b = alpha / v and a = 1 - alpha m1 / v.  With m_n = <H^n> (m4 = <H^4>),
+ *   <phi|H^k|phi> / <psi0|psi0> = a^2 m_k + 2 a b m_{k+1} + b^2 m_{k+2},
+ * so E1 = <H>_phi and var1 = <H^2>_phi - E1^2; the p = 0 point is (m1,
+ * var0 = m2 - m1^2).  The straight line through (var0, m1) and (var1, E1)
+ * is evaluated at zero variance (equal variances: E1).
+ * m: m0..m4 (m0 = 1); lz: {E_p1, v, alpha}.  out = {var0, E1, var1, E_extrap}. */
+void or_lanczos_variance(const double *m, const double *lz, double *out)
+{
+    const double m1 = m[1], m2 = m[2], m3 = m[3], m4 = m[4];
+    const double v = lz[1], alpha = lz[2];
+    const double var0 = m2 - m1 * m1;
+    double a = 1.0, b = 0.0;
+    if (v > 0.0) { b = alpha / v; a = 1.0 - alpha * m1 / v; }
+    const double n0 = a * a + 2 * a * b * m1 + b * b * m2;
+    const double n1 = a * a * m1 + 2 * a * b * m2 + b * b * m3;
+    const double n2 = a * a * m2 + 2 * a * b * m3 + b * b * m4;
+    const double E1 = n1 / n0, var1 = n2 / n0 - E1 * E1;
+    out[0] = var0;
+    out[1] = E1;
+    out[2] = var1;
+    out[3] = var0 != var1 ? E1 - var1 * (m1 - E1) / (var0 - var1) : E1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Static spin structure factor (Sec. 4.1)                                    */
+/* ------------------------------------------------------------------------ */
+
+/* S(q) = (1/N^2) sum_{i,j} <sz_i sz_j> e^{i q.(r_i - r_j)}, sz = s/2, for
+ * every q = 2 pi (qx, qy) / L (out index qx + L qy), as the weighted mean of
+ * the diagonal estimator over the configurations (weights NULL: plain mean).
+ * Written as the double sum over site pairs; the imaginary parts cancel
+ * between (i, j) and (j, i), so only the cosine is summed. */
+void or_structure_factor(int L, const int8_t *spins, int n, const double *weights, double *out)
+{
+    const int N = L * L;
+    double *acc = (double *)calloc((size_t)N, sizeof(double));
+    double z = 0;
+    for (int k = 0; k < n; ++k) z += weights ? weights[k] : 1.0;
+    #pragma omp parallel for schedule(static)
+    for (int q = 0; q < N; ++q) {
+        const int qx = q % L, qy = q / L;
+        double sum = 0;
+        for (int k = 0; k < n; ++k) {
+            const int8_t *s = spins + (size_t)k * N;
+            double t = 0;
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j) {
+                    const int dx = i % L - j % L, dy = i / L - j / L;
+                    t += 0.25 * s[i] * s[j] * cos(2.0 * M_PI * (qx * dx + qy * dy) / L);
+                }
+            sum += (weights ? weights[k] : 1.0) * t;
+        }
+        acc[q] = sum;
+    }
+    for (int q = 0; q < N; ++q) out[q] = acc[q] / (z * (double)N * (double)N);
+    free(acc);
 }
 
 /* ------------------------------------------------------------------------ */

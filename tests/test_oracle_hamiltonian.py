@@ -160,3 +160,52 @@ def test_apply_h_matches_kron():
     H, _ = H_sz0()
     x = np.random.default_rng(4).normal(size=st.size)
     np.testing.assert_allclose(oracle.apply_h(L, 1.0, J2, st, x), H @ x, rtol=1e-12, atol=1e-12)
+
+
+def test_fourth_moment_and_p1_variance_exact():
+    # m4 = <|h2|^2> under exact weights equals psi^T H^4 psi / psi^T psi; the
+    # p = 1 state's energy and variance from the moments equal those of the
+    # explicit vector phi = psi0 + alpha (H - m1) psi0 / v built with the
+    # Kronecker Hamiltonian; E1 equals the closed-form E_p1.
+    m = _model(False, M=4, seed=10, std=0.3)
+    psi = _psi_all(m)
+    H, _ = H_sz0()
+    _, s = basis()
+    h1, h2 = m.lanczos_h(s)
+    mo = oracle.moments(h1, h2, np.abs(psi) ** 2)
+    nrm = np.vdot(psi, psi).real
+    v2 = H @ (H @ psi)
+    np.testing.assert_allclose(mo["m4"], np.vdot(v2, v2).real / nrm, rtol=1e-12)
+    m5 = np.concatenate([mo["m"], [mo["m4"]]])
+    lz = oracle.lanczos_step(mo["m"])
+    var = oracle.lanczos_variance(m5, lz)
+    phi = psi + lz["alpha"] * (H @ psi - m5[1] * psi) / lz["v"]
+    hphi = H @ phi
+    pn = np.vdot(phi, phi).real
+    E1 = np.vdot(phi, hphi).real / pn
+    var1 = np.vdot(hphi, hphi).real / pn - E1 ** 2
+    assert abs(var["E1"] - E1) < 1e-10 * abs(E1)
+    assert abs(var["E1"] - lz["E"]) < 1e-10 * abs(E1)
+    assert abs(var["var1"] - var1) < 1e-8 * abs(var1)
+    assert abs(var["var0"] - (m5[2] - m5[1] ** 2)) < 1e-12 * m5[2]
+    assert 0 < var["var1"] < var["var0"]          # a Lanczos step lowers the variance
+    # the extrapolated energy lies on the line through both points, at zero variance
+    slope = (m5[1] - var["E1"]) / (var["var0"] - var["var1"])
+    assert abs(var["E_extrap"] - (var["E1"] - slope * var["var1"])) < 1e-12 * abs(E1)
+
+
+def test_variance_of_an_eigenstate_vanishes():
+    # the ED ground state: zero variance at p = 0 and p = 1, E_extrap = E0
+    H, _ = H_sz0(0.0)
+    E0, vec = spla.eigsh(H, k=1, which="SA", tol=1e-14)
+    v = vec[:, 0] / np.linalg.norm(vec[:, 0])
+    # moments of the eigenvector from repeated matvecs
+    m, x = [1.0], v
+    for _ in range(4):
+        y = H @ x
+        m.append(np.vdot(v, y).real)
+        x = y
+    lz = oracle.lanczos_step(m[:4])
+    var = oracle.lanczos_variance(m, lz)
+    assert lz["alpha"] == 0.0 and abs(var["var0"]) <= 1e-12 * E0[0] ** 2
+    assert abs(var["E1"] - E0[0]) < 1e-12 * abs(E0[0]) and abs(var["E_extrap"] - E0[0]) < 1e-9 * abs(E0[0])
