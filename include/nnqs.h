@@ -156,7 +156,7 @@ int nnqs_local_energy(nnqs_model *model, const uint64_t *cfg, int64_t n, double 
  * |psi|^2 the FP64 moments
  *   moments_out[0..7] = {m0 = 1, m1 = <Re h1>, m2 = <|h1|^2>,
  *                        m3 = <Re(conj(h1) h2)>, n, <Im h1>,
- *                        <Im(conj(h1) h2)>, 0}
+ *                        <Im(conj(h1) h2)>, m4 = <|h2|^2>}
  * and the p = 1 energy lanczos_out[0..2] = {E_p1, v, alpha} of the 2x2
  * problem in span{psi0, psi1}:  v^2 = m2 - m1^2,
  * d = (m3 - 3 m1 m2 + 2 m1^3) / (2 v^3), alpha = d - sqrt(d^2 + 1),
@@ -164,6 +164,28 @@ int nnqs_local_energy(nnqs_model *model, const uint64_t *cfg, int64_t n, double 
  * moments_out and lanczos_out are device buffers (either may be NULL). */
 int nnqs_lanczos_moments(nnqs_model *model, const uint64_t *cfg, int64_t n, double *h1_out,
                          double *h2_out, double *moments_out, double *lanczos_out, void *stream);
+
+/* Energy variance of the p = 0 and p = 1 states and the variance
+ * extrapolation (Sec. 3.3 Eq. 16; Sec. 4.3), in FP64 on the device.  The p = 1
+ * state is phi = psi0 + alpha psi1, psi1 = (H - m1) psi0 / v, i.e.
+ * a psi0 + b H psi0 with b = alpha / v, a = 1 - alpha m1 / v, so that
+ * <phi|H^k|phi> = a^2 m_k + 2ab m_{k+1} + b^2 m_{k+2} (k = 0, 1, 2):
+ *   out[0..3] = {var0 = m2 - m1^2, E1 = <H>_phi, var1 = <H^2>_phi - E1^2,
+ *                E_extrap},
+ * E_extrap being the straight line through (var0, m1) and (var1, E1) at zero
+ * variance (E1 if the variances are equal).  moments: the [8] output of
+ * nnqs_lanczos_moments (m0..m3 and m4 = moments[7]); lanczos: its [3]
+ * output; out: [4].  All device buffers; no model is needed. */
+int nnqs_lanczos_variance(const double *moments, const double *lanczos, double *out, void *stream);
+
+/* Static spin structure factor (Sec. 4.1):
+ *   S(q) = (1/N^2) sum_{i,j} <sz_i sz_j> e^{i q.(r_i - r_j)},  sz = s/2,
+ * for all N wave vectors q = 2 pi (qx, qy) / L, sq_out[qx + L qy] (FP64), as
+ * the mean over the n configurations of the diagonal estimator
+ * (1/N^2) |sum_j sz_j e^{i q.r_j}|^2 (weights: optional device [n], a
+ * weighted mean; NULL = plain mean of |psi|^2 samples).  n >= 1. */
+int nnqs_structure_factor(nnqs_model *model, const uint64_t *cfg, int64_t n, const double *weights,
+                          double *sq_out, void *stream);
 
 /* Log-derivatives O_k(s) = d log psi(s) / d alpha_k (holomorphic; Sec. 3.2,
  * after Eq. 12), in parameter order.  O_out: [n][P][2] doubles. */

@@ -405,7 +405,7 @@ int nnqs_local_energy(nnqs_model *m, const uint64_t *cfg, int64_t n, double *elo
         if (e != cudaSuccess) return cuda_fail(e, "local_energy");
         if (sums) {
             const int nb = 64;
-            int rc = ensure_ws(m, nb * 6 * sizeof(double));
+            int rc = ensure_ws(m, nb * kMomentSums * sizeof(double));
             if (rc) return rc;
             e = launch_eloc_sums(eloc, n, (double *)m->ws, nb, sums, st);
             if (e != cudaSuccess) return cuda_fail(e, "eloc sums");
@@ -424,7 +424,7 @@ int nnqs_lanczos_moments(nnqs_model *m, const uint64_t *cfg, int64_t n, double *
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
         const int nb = 64;
-        size_t need = align256(nb * 6 * sizeof(double));
+        size_t need = align256(nb * kMomentSums * sizeof(double));
         const size_t off_h1 = need;
         if (!h1) need += align256((size_t)n * 2 * sizeof(double));
         const size_t off_h2 = need;
@@ -548,12 +548,12 @@ int nnqs_sr_solve(const nnqs_model *mc, const double *O, const double *weights, 
 
 // ---------------------------------------------------------------------------
 // Fixed-size scratch of nnqs_lanczos_moments_noalloc: h1 [max][2], h2 [max][2]
-// and the FP64 partial sums [kNoallocBlocks][6].  In host code the array's
+// and the FP64 partial sums [kNoallocBlocks][kMomentSums].  In host code the array's
 // name is only a stand-in; its device address is looked up once per device.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kNoallocBlocks = 64;
-constexpr size_t kNoallocDoubles = (size_t)4 * NNQS_NOALLOC_MAX_SAMPLES + (size_t)kNoallocBlocks * 6;
+constexpr size_t kNoallocDoubles = (size_t)4 * NNQS_NOALLOC_MAX_SAMPLES + (size_t)kNoallocBlocks * kMomentSums;
 }  // namespace
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
@@ -604,6 +604,29 @@ int nnqs_lanczos_moments_noalloc(nnqs_model *m, const uint64_t *cfg, int64_t n, 
             if (e != cudaSuccess) return cuda_fail(e, "moments (fixed scratch)");
         }
         return NNQS_OK;
+    });
+}
+
+int nnqs_lanczos_variance(const double *moments, const double *lanczos, double *out, void *stream)
+{
+    if (!moments || !lanczos || !out) return fail(NNQS_EINVAL, "moments, lanczos and out must be non-NULL");
+    const cudaError_t e = launch_lanczos_variance(moments, lanczos, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "lanczos_variance");
+}
+
+int nnqs_structure_factor(nnqs_model *m, const uint64_t *cfg, int64_t n, const double *weights, double *sq_out,
+                          void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n < 1) return fail(NNQS_EINVAL, "n must be >= 1");
+    if (!cfg || !sq_out) return fail(NNQS_EINVAL, "cfg and sq_out must be non-NULL");
+    return with_device(m, [&]() -> int {
+        const int grid = sq_grid(n, m->nsm);
+        int rc = ensure_ws(m, (size_t)grid * (m->N + 1) * sizeof(double));
+        if (rc) return rc;
+        const cudaError_t e = launch_structure_factor(cfg, n, m->d.L, m->nwords, weights, (double *)m->ws, grid,
+                                                      sq_out, (cudaStream_t)stream);
+        return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "structure_factor");
     });
 }
 

@@ -112,10 +112,10 @@ __global__ void __launch_bounds__(256) k_moments_batched(const double *__restric
                                                          const int64_t *__restrict__ out_off,
                                                          double *__restrict__ moments, double *__restrict__ lanczos)
 {
-    __shared__ double sh[8][6];
+    __shared__ double sh[8][kMomentSums];
     const int mi = blockIdx.x;
     const int64_t lo = out_off[mi], hi = out_off[mi + 1];
-    double v[6] = {0, 0, 0, 0, 0, 0};
+    double v[kMomentSums] = {0, 0, 0, 0, 0, 0, 0};
     for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
         const double ax = h1_all[2 * k], ay = h1_all[2 * k + 1], bx = h2_all[2 * k], by = h2_all[2 * k + 1];
         v[0] += 1.0;
@@ -124,23 +124,24 @@ __global__ void __launch_bounds__(256) k_moments_batched(const double *__restric
         v[3] += ax * bx + ay * by;  // Re(conj(h1) h2)
         v[4] += ay;
         v[5] += ax * by - ay * bx;  // Im(conj(h1) h2)
+        v[6] += bx * bx + by * by;  // |h2|^2
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < 6; ++q)
+    for (int q = 0; q < kMomentSums; ++q)
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     if (lane == 0)
-        for (int q = 0; q < 6; ++q) sh[warp][q] = v[q];
+        for (int q = 0; q < kMomentSums; ++q) sh[warp][q] = v[q];
     __syncthreads();
     if (threadIdx.x != 0) return;
     for (int w = 1; w < 8; ++w)
-        for (int q = 0; q < 6; ++q) sh[0][q] += sh[w][q];
+        for (int q = 0; q < kMomentSums; ++q) sh[0][q] += sh[w][q];
     const double z = sh[0][0] > 0 ? sh[0][0] : 1.0;
     const double m1 = sh[0][1] / z, m2 = sh[0][2] / z, m3 = sh[0][3] / z;
     if (moments) {
         double *mo = moments + 8 * mi;
         mo[0] = 1.0; mo[1] = m1; mo[2] = m2; mo[3] = m3;
-        mo[4] = sh[0][0]; mo[5] = sh[0][4] / z; mo[6] = sh[0][5] / z; mo[7] = 0.0;
+        mo[4] = sh[0][0]; mo[5] = sh[0][4] / z; mo[6] = sh[0][5] / z; mo[7] = sh[0][6] / z;
     }
     if (lanczos) lanczos_p1(m1, m2, m3, lanczos + 3 * mi);
 }

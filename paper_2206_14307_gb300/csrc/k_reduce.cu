@@ -32,10 +32,10 @@ __global__ void __launch_bounds__(kRedThreads) k_moments_partial(const double *_
                                                                  const double *__restrict__ h2, int64_t n,
                                                                  double *__restrict__ partial)
 {
-    __shared__ double sh[kRedThreads / 32][6];
+    __shared__ double sh[kRedThreads / 32][kMomentSums];
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t lo = per * blockIdx.x, hi = lo + per < n ? lo + per : n;
-    double v[6] = {0, 0, 0, 0, 0, 0};
+    double v[kMomentSums] = {0, 0, 0, 0, 0, 0, 0};
     for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
         const double ax = h1[2 * k], ay = h1[2 * k + 1];
         v[0] += 1.0;
@@ -46,11 +46,12 @@ __global__ void __launch_bounds__(kRedThreads) k_moments_partial(const double *_
             const double bx = h2[2 * k], by = h2[2 * k + 1];
             v[3] += ax * bx + ay * by;   // Re(conj(h1) h2)
             v[5] += ax * by - ay * bx;   // Im(conj(h1) h2)
+            v[6] += bx * bx + by * by;   // |h2|^2
         }
     }
-    block_sum<6>(v, sh);
+    block_sum<kMomentSums>(v, sh);
     if (threadIdx.x == 0)
-        for (int q = 0; q < 6; ++q) partial[blockIdx.x * 6 + q] = v[q];
+        for (int q = 0; q < kMomentSums; ++q) partial[blockIdx.x * kMomentSums + q] = v[q];
 }
 
 // stage 2: fixed-order sum of the partials, moments and the p = 1 Lanczos step
@@ -58,14 +59,14 @@ __global__ void __launch_bounds__(32) k_moments_final(const double *__restrict__
                                                       double *__restrict__ moments, double *__restrict__ lanczos)
 {
     if (threadIdx.x != 0) return;
-    double v[6] = {0, 0, 0, 0, 0, 0};
+    double v[kMomentSums] = {0, 0, 0, 0, 0, 0, 0};
     for (int b = 0; b < nb; ++b)
-        for (int q = 0; q < 6; ++q) v[q] += partial[b * 6 + q];
+        for (int q = 0; q < kMomentSums; ++q) v[q] += partial[b * kMomentSums + q];
     const double z = v[0] > 0 ? v[0] : 1.0;
     const double m1 = v[1] / z, m2 = v[2] / z, m3 = v[3] / z;
     if (moments) {
         moments[0] = 1.0; moments[1] = m1; moments[2] = m2; moments[3] = m3;
-        moments[4] = v[0]; moments[5] = v[4] / z; moments[6] = v[5] / z; moments[7] = 0.0;
+        moments[4] = v[0]; moments[5] = v[4] / z; moments[6] = v[5] / z; moments[7] = v[6] / z;
     }
     if (lanczos) lanczos_p1(m1, m2, m3, lanczos);
 }
@@ -81,9 +82,9 @@ cudaError_t launch_moments(const double *h1, const double *h2, int64_t n, double
 __global__ void __launch_bounds__(32) k_eloc_final(const double *__restrict__ partial, int nb, double *__restrict__ sums)
 {
     if (threadIdx.x != 0) return;
-    double v[6] = {0, 0, 0, 0, 0, 0};
+    double v[kMomentSums] = {0, 0, 0, 0, 0, 0, 0};
     for (int b = 0; b < nb; ++b)
-        for (int q = 0; q < 6; ++q) v[q] += partial[b * 6 + q];
+        for (int q = 0; q < kMomentSums; ++q) v[q] += partial[b * kMomentSums + q];
     sums[0] = v[1]; sums[1] = v[4]; sums[2] = v[2]; sums[3] = v[0];
 }
 

@@ -26,6 +26,16 @@ template <typename T>
 cudaError_t launch_ratio_variant(const DevModel<T> &md, int v, const uint64_t *cfg, int64_t n, int mode, double *h1,
                                  double *h2, int nsm, cudaStream_t st);
 
+// FP64 per-block partial sums of the moment reduction: n, Re h1, |h1|^2,
+// Re(conj h1 h2), Im h1, Im(conj h1 h2), |h2|^2
+constexpr int kMomentSums = 7;
+
+// observables: structure factor partial sums [grid][N + 1] and the p = 1 variance
+int sq_grid(int64_t n, int nsm);
+cudaError_t launch_structure_factor(const uint64_t *cfg, int64_t n, int L, int nwords, const double *weights,
+                                    double *partial, int grid, double *sq_out, cudaStream_t st);
+cudaError_t launch_lanczos_variance(const double *moments, const double *lanczos, double *out, cudaStream_t st);
+
 // Mixed batch (Lanczos mode): one persistent launch over (instance, sample)
 // items; each instance runs with its own tile shape (GL lanes per row, MPL
 // hidden units per lane).

@@ -30,7 +30,7 @@ ABI_FUNCTIONS = (
     "nnqs_status", "nnqs_last_error", "nnqs_lanczos_moments_noalloc", "nnqs_sr_solve",
     "nnqs_num_tile_shapes", "nnqs_tile_shape", "nnqs_batch_create", "nnqs_batch_destroy", "nnqs_batch_size",
     "nnqs_batch_model", "nnqs_batch_get_shape", "nnqs_batch_set_shape", "nnqs_batch_autotune",
-    "nnqs_batch_lanczos", "nnqs_batch_status",
+    "nnqs_batch_lanczos", "nnqs_batch_status", "nnqs_lanczos_variance", "nnqs_structure_factor",
 )
 NOALLOC_MAX_SAMPLES = 65536
 
@@ -80,6 +80,8 @@ def lib():
             "nnqs_status": ([P, P], ctypes.c_int),
             "nnqs_lanczos_moments_noalloc": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_last_error": ([], ctypes.c_char_p),
+            "nnqs_lanczos_variance": ([P, P, P, P], ctypes.c_int),
+            "nnqs_structure_factor": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_num_tile_shapes": ([], i32),
             "nnqs_tile_shape": ([i32, P, P], ctypes.c_int),
             "nnqs_batch_create": ([P, i32, ctypes.POINTER(P)], ctypes.c_int),
@@ -149,6 +151,14 @@ def nnqs_status(h, stream=0): return _check(lib().nnqs_status(h, stream))
 
 def nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream=0):
     return _check(lib().nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream))
+
+
+def nnqs_lanczos_variance(moments, lanczos, out, stream=0):
+    return _check(lib().nnqs_lanczos_variance(moments, lanczos, out, stream))
+
+
+def nnqs_structure_factor(h, cfg, n, weights, sq_out, stream=0):
+    return _check(lib().nnqs_structure_factor(h, cfg, n, weights, sq_out, stream))
 
 
 def nnqs_num_tile_shapes(): return lib().nnqs_num_tile_shapes()
@@ -305,8 +315,22 @@ class Model:
                       float(tol), delta.data_ptr(), info.data_ptr(), _ptr(params_inout), _stream())
         return delta, info
 
+    def structure_factor(self, cfg, weights=None, out=None):
+        """S(q) [N] for q = 2 pi (qx, qy)/L at index qx + L qy."""
+        out = self._out(self.N) if out is None else out
+        nnqs_structure_factor(self.h, cfg.data_ptr(), cfg.shape[0], _ptr(weights), out.data_ptr(), _stream())
+        return out
+
     def status(self):
         return nnqs_status(self.h, _stream())
+
+
+def lanczos_variance(moments, lanczos, out=None):
+    """{var0, E1, var1, E_extrap} on the device from the [8] moments and [3] step."""
+    import torch
+    out = torch.empty(4, dtype=torch.float64, device="cuda") if out is None else out
+    nnqs_lanczos_variance(moments.data_ptr(), lanczos.data_ptr(), out.data_ptr(), _stream())
+    return out
 
 
 def cfg_tensor(words: np.ndarray):

@@ -106,6 +106,7 @@ def test_small_mixed_batch_matches_oracle():
         # the batched FP64 reduction of the kernel's own h1, h2
         m, l = _moments_host(H1[i], H2[i])
         assert mo[i][4] == SMALL_COUNTS[i]
+        assert abs(mo[i][7] - np.mean(np.abs(H2[i]) ** 2)) <= 1e-12 * mo[i][7]   # m4
         np.testing.assert_allclose(mo[i][:4], m[:4], rtol=1e-12, atol=1e-14)
         _assert_lanczos_close(lz[i], mo[i])
         # and the oracle's moments (E_p1 of a handful of random configurations
