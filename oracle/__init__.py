@@ -58,6 +58,9 @@ def lib():
         L.or_moments.argtypes = [i, P, P, P, P]
         L.or_lanczos_step.argtypes = [P, P]
         L.or_lanczos_variance.argtypes = [P, P, P]
+        L.or_lanczos_h3.argtypes = [P, P, i, P, P, P]
+        L.or_shifted_moments.argtypes = [i, P, P, P, d, P, P]
+        L.or_krylov2.argtypes = [P, d, P]
         L.or_structure_factor.argtypes = [i, P, i, P, P]
         L.or_energy_grad.argtypes = [i, i, P, P, P, P]
         L.or_sr_solve.argtypes = [i, i, P, P, d, d, P]
@@ -168,6 +171,14 @@ class Model:
         lib().or_lanczos_h(self._h, _p(s), s.shape[0], _p(h1), _p(h2))
         return h1[:, 0] + 1j * h1[:, 1], h2[:, 0] + 1j * h2[:, 1]
 
+    def lanczos_h3(self, s):
+        """(h1, h2, h3) with h3 = (H^3 psi)/psi by triple enumeration."""
+        s = self._spins(s)
+        n = len(s)
+        a, b, c = np.zeros((n, 2)), np.zeros((n, 2)), np.zeros((n, 2))
+        lib().or_lanczos_h3(self._h, _p(s), n, _p(a), _p(b), _p(c))
+        return a[:, 0] + 1j * a[:, 1], b[:, 0] + 1j * b[:, 1], c[:, 0] + 1j * c[:, 1]
+
     def grad_logpsi(self, s):
         s = self._spins(s)
         out = np.zeros((s.shape[0], self.P, 2))
@@ -214,6 +225,24 @@ def lanczos_variance(m, lz):
     out = np.zeros(4)
     lib().or_lanczos_variance(_p(mm), _p(ll), _p(out))
     return dict(var0=out[0], E1=out[1], var1=out[2], E_extrap=out[3])
+
+
+def shifted_moments(h1, h2, h3, c, weights=None):
+    """mu_0..mu_6 of (H - c) from the local h1, h2, h3; returns (mu[7], sum of weights)."""
+    cols = [np.ascontiguousarray(np.stack([np.real(x), np.imag(x)], -1).astype(np.float64)) for x in (h1, h2, h3)]
+    w = None if weights is None else np.ascontiguousarray(np.asarray(weights, np.float64))
+    out = np.zeros(8)
+    lib().or_shifted_moments(len(cols[0]), _p(cols[0]), _p(cols[1]), _p(cols[2]), float(c),
+                             _p(w) if w is not None else None, _p(out))
+    return out[:7].copy(), out[7]
+
+
+def krylov2(mu, c):
+    """p = 2 step from mu_0..mu_6 about c: dict E, x (coefficients of (H-c)^i psi0, x0 = 1), var."""
+    mu = np.ascontiguousarray(np.asarray(mu, np.float64)[:7])
+    out = np.zeros(5)
+    lib().or_krylov2(_p(mu), float(c), _p(out))
+    return dict(E=out[0], x=out[1:4].copy(), var=out[4])
 
 
 def structure_factor(L, spins, weights=None):

@@ -21,6 +21,8 @@
  *   - Moments <H^n>, n<=4, and the p=1 Lanczos energy, Eqs. 13-18, with the
  *     closed form re-derived from the 2x2 matrix in span{psi0, psi1}; the
  *     p=1 state's variance and the variance extrapolation (Sec. 4.3).
+ *   - The p=2 step: (H^3 psi)/psi by triple enumeration, moments about a
+ *     shift up to order 6, the 3x3 Krylov pencil (Cholesky + Jacobi).
  *   - Static spin structure factor S(q) (Sec. 4.1) as the double sum over
  *     site pairs.
  *   - Log-derivatives O_k and the SR system, Eq. 12.
@@ -365,6 +367,64 @@ void or_lanczos_h(void *hp, const int8_t *spins, int n, double *h1out, double *h
     }
 }
 
+/* (H^2 psi)(s)/psi(s) of one configuration by double enumeration, serial:
+ * diag(s) h1(s) + sum_{s'} (J/2) [psi(s')/psi(s)] h1(s'), h1 = eloc_one. */
+static cplx h2_one(const or_model *h, const int8_t *s, cplx lp, cplx h1)
+{
+    int8_t *sp = (int8_t *)malloc(h->N);
+    cplx acc = diag_energy(h, s) * h1;
+    for (int b = 0; b < h->nb; ++b) {
+        int i = h->bi[b], j = h->bj[b];
+        if (s[i] == s[j]) continue;
+        double J = h->bt[b] == 1 ? h->J1 : h->J2;
+        memcpy(sp, s, h->N);
+        sp[i] = s[j]; sp[j] = s[i];
+        cplx lpp = log_psi_one(h, sp);
+        acc += 0.5 * J * cexp(lpp - lp) * eloc_one(h, sp, lpp);
+    }
+    free(sp);
+    return acc;
+}
+
+/* The p = 2 quantities (Sec. 3.3, |Psi_2> = (1 + beta_1 H + beta_2 H^2)
+ * |psi0>): h1, h2 and h3 = (H^3 psi)(s)/psi(s) = diag(s) h2(s) +
+ * sum_{s'} (J/2) [psi(s')/psi(s)] h2(s') by explicit triple enumeration,
+ * every psi from scratch.  The first-level neighbours run in parallel. */
+void or_lanczos_h3(void *hp, const int8_t *spins, int n, double *h1out, double *h2out, double *h3out)
+{
+    const or_model *h = (const or_model *)hp;
+    const int N = h->N;
+    for (int k = 0; k < n; ++k) {
+        const int8_t *s = spins + (size_t)k * N;
+        const cplx lp = log_psi_one(h, s);
+        const cplx h1 = eloc_one(h, s, lp);
+        const cplx h2 = h2_one(h, s, lp, h1);
+        cplx acc = diag_energy(h, s) * h2;
+        #pragma omp parallel
+        {
+            int8_t *sp = (int8_t *)malloc(N);
+            cplx part = 0;
+            #pragma omp for schedule(dynamic)
+            for (int b = 0; b < h->nb; ++b) {
+                int i = h->bi[b], j = h->bj[b];
+                if (s[i] == s[j]) continue;
+                double J = h->bt[b] == 1 ? h->J1 : h->J2;
+                memcpy(sp, s, N);
+                sp[i] = s[j]; sp[j] = s[i];
+                const cplx lpp = log_psi_one(h, sp);
+                const cplx h1p = eloc_one(h, sp, lpp);
+                part += 0.5 * J * cexp(lpp - lp) * h2_one(h, sp, lpp, h1p);
+            }
+            #pragma omp critical
+            acc += part;
+            free(sp);
+        }
+        h1out[2 * k] = creal(h1); h1out[2 * k + 1] = cimag(h1);
+        h2out[2 * k] = creal(h2); h2out[2 * k + 1] = cimag(h2);
+        h3out[2 * k] = creal(acc); h3out[2 * k + 1] = cimag(acc);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Moments and the p = 1 Lanczos step (Eqs. 13-18)                           */
 /* ------------------------------------------------------------------------ */
@@ -451,6 +511,119 @@ void or_lanczos_variance(const double *m, const double *lz, double *out)
     out[1] = E1;
     out[2] = var1;
     out[3] = var0 != var1 ? E1 - var1 * (m1 - E1) / (var0 - var1) : E1;
+}
+
+/* Moments about a shift c, mu_k = <psi|(H - c)^k|psi>/<psi|psi> for k = 0..6,
+ * from the local quantities a_0 = 1, a_1 = h1 - c, a_2 = h2 - 2c h1 + c^2,
+ * a_3 = h3 - 3c h2 + 3c^2 h1 - c^3 (a_i = ((H - c)^i psi)(s)/psi(s)):
+ * mu_{i+j} = <Re(conj(a_i) a_j)> with (i, j) = (0,0), (0,1), (1,1), (1,2),
+ * (2,2), (2,3), (3,3).  Weighted means (weights NULL: plain means), summed
+ * pairwise.  out[0..6] = mu_0..mu_6, out[7] = sum of weights. */
+void or_shifted_moments(int n, const double *h1, const double *h2, const double *h3, double c,
+                        const double *weights, double *out)
+{
+    double *col = (double *)malloc(sizeof(double) * 8 * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+        const double w = weights ? weights[k] : 1.0;
+        const cplx x1 = h1[2 * k] + I * h1[2 * k + 1];
+        const cplx x2 = h2[2 * k] + I * h2[2 * k + 1];
+        const cplx x3 = h3[2 * k] + I * h3[2 * k + 1];
+        const cplx a1 = x1 - c;
+        const cplx a2 = x2 - 2 * c * x1 + c * c;
+        const cplx a3 = x3 - 3 * c * x2 + 3 * c * c * x1 - c * c * c;
+        const double v[8] = {w, w * creal(a1), w * creal(conj(a1) * a1), w * creal(conj(a1) * a2),
+                             w * creal(conj(a2) * a2), w * creal(conj(a2) * a3), w * creal(conj(a3) * a3), w};
+        for (int q = 0; q < 8; ++q) col[(size_t)q * n + k] = v[q];
+    }
+    const double z = pairwise(col, n);
+    for (int q = 0; q < 7; ++q) out[q] = pairwise(col + (size_t)q * n, n) / z;
+    out[7] = z;
+    free(col);
+}
+
+/* The p = 2 Lanczos step (Sec. 3.3): the lowest eigenpair of the pencil
+ * A x = lambda B x with A_ij = mu_{i+j+1}, B_ij = mu_{i+j} (i, j = 0..2), the
+ * Hamiltonian about c and the overlap in the Krylov basis {psi0, (H - c)psi0,
+ * (H - c)^2 psi0} (the Krylov space, and so E, does not depend on c).
+ * B = L L^T (Cholesky), C = L^{-1} A L^{-T}, cyclic Jacobi rotations on C,
+ * x = L^{-T} y for the lowest eigenvector y, scaled so that x0 = 1.
+ * out = {E_p2 = c + lambda, x0, x1, x2, var_p2} with
+ * var_p2 = sum x_i x_j mu_{i+j+2} / sum x_i x_j mu_{i+j} - lambda^2. */
+void or_krylov2(const double *mu, double c, double *out)
+{
+    double A[3][3], B[3][3], Lm[3][3] = {{0}}, Li[3][3] = {{0}}, C[3][3], T[3][3], V[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) { A[i][j] = mu[i + j + 1]; B[i][j] = mu[i + j]; }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double t = B[i][j];
+            for (int k = 0; k < j; ++k) t -= Lm[i][k] * Lm[j][k];
+            Lm[i][j] = i == j ? sqrt(t) : t / Lm[j][j];
+        }
+    for (int j = 0; j < 3; ++j) {            /* Li = L^{-1} by forward substitution */
+        for (int i = 0; i < 3; ++i) {
+            double t = i == j ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= Lm[i][k] * Li[k][j];
+            Li[i][j] = t / Lm[i][i];
+        }
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double t = 0;
+            for (int k = 0; k < 3; ++k) t += Li[i][k] * A[k][j];
+            T[i][j] = t;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double t = 0;
+            for (int k = 0; k < 3; ++k) t += T[i][k] * Li[j][k];
+            C[i][j] = t;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = i == j;
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = fabs(C[0][1]) + fabs(C[0][2]) + fabs(C[1][2]);
+        if (off < 1e-300) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (C[p][q] == 0.0) continue;
+                const double th = (C[q][q] - C[p][p]) / (2 * C[p][q]);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1));
+                const double cs = 1 / sqrt(t * t + 1), sn = t * cs;
+                for (int k = 0; k < 3; ++k) {      /* C <- J^T C J */
+                    const double ckp = C[k][p], ckq = C[k][q];
+                    C[k][p] = cs * ckp - sn * ckq;
+                    C[k][q] = sn * ckp + cs * ckq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double cpk = C[p][k], cqk = C[q][k];
+                    C[p][k] = cs * cpk - sn * cqk;
+                    C[q][k] = sn * cpk + cs * cqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = cs * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    int lo = 0;
+    for (int i = 1; i < 3; ++i)
+        if (C[i][i] < C[lo][lo]) lo = i;
+    const double lam = C[lo][lo];
+    double x[3];
+    for (int i = 0; i < 3; ++i) {                 /* x = L^{-T} y */
+        double t = 0;
+        for (int k = 0; k < 3; ++k) t += Li[k][i] * V[k][lo];
+        x[i] = t;
+    }
+    for (int i = 2; i >= 0; --i) x[i] /= x[0];
+    double n0 = 0, n2 = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) { n0 += x[i] * x[j] * mu[i + j]; n2 += x[i] * x[j] * mu[i + j + 2]; }
+    out[0] = c + lam;
+    out[1] = x[0]; out[2] = x[1]; out[3] = x[2];
+    out[4] = n2 / n0 - lam * lam;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -5,6 +5,7 @@ import functools
 import numpy as np
 import pytest
 import scipy.linalg
+import scipy.sparse
 import scipy.sparse.linalg as spla
 
 import oracle
@@ -209,3 +210,70 @@ def test_variance_of_an_eigenstate_vanishes():
     var = oracle.lanczos_variance(m, lz)
     assert lz["alpha"] == 0.0 and abs(var["var0"]) <= 1e-12 * E0[0] ** 2
     assert abs(var["E1"] - E0[0]) < 1e-12 * abs(E0[0]) and abs(var["E_extrap"] - E0[0]) < 1e-9 * abs(E0[0])
+
+
+def test_h3_equals_H3_psi_over_psi():
+    for proj, M, seed in ((False, 5, 11), (True, 4, 12)):
+        m = _model(proj, M=M, seed=seed)
+        psi = _psi_all(m)
+        H, _ = H_sz0()
+        v1 = H @ psi
+        v2 = H @ v1
+        v3 = H @ v2
+        _, s = basis()
+        sel = np.random.default_rng(2).choice(len(s), 6 if proj else 12, replace=False)
+        sel = sel[np.abs(psi[sel]) > 1e-6 * np.abs(psi).max()]
+        h1, h2, h3 = m.lanczos_h3(s[sel])
+        np.testing.assert_allclose(h1, v1[sel] / psi[sel], rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(h2, v2[sel] / psi[sel], rtol=1e-10, atol=1e-9)
+        np.testing.assert_allclose(h3, v3[sel] / psi[sel], rtol=1e-10, atol=1e-8)
+
+
+def test_p2_krylov_step_exact():
+    # exact-weight shifted moments = psi^T (H - c)^k psi / psi^T psi (k <= 6);
+    # the 3x3 pencil's lowest eigenvalue = scipy's generalized eigensolve =
+    # Rayleigh-Ritz in span{psi, H psi, H^2 psi}; E0 <= E_p2 <= E_p1; the
+    # variance of the p = 2 state equals that of the explicit vector.
+    m = _model(False, M=4, seed=13, std=0.3)
+    psi = _psi_all(m)
+    H, _ = H_sz0()
+    _, s = basis()
+    # h3 of the whole sector from dense matvecs would test nothing new; the
+    # oracle's triple enumeration is pinned above, so exact weights use it on a
+    # subset and the dense vectors for the identities on the full sector
+    nrm = np.vdot(psi, psi).real
+    c = np.vdot(psi, H @ psi).real / nrm
+    Hc = H - c * scipy.sparse.identity(H.shape[0], format="csr")
+    vs = [psi]
+    for _ in range(3):
+        vs.append(Hc @ vs[-1])
+    mu_exact = [np.vdot(vs[i], vs[j]).real / nrm for i, j in ((0, 0), (0, 1), (1, 1), (1, 2), (2, 2), (2, 3), (3, 3))]
+    h1 = (H @ psi) / psi
+    h2 = (H @ (H @ psi)) / psi
+    h3 = (H @ (H @ (H @ psi))) / psi
+    mu, z = oracle.shifted_moments(h1, h2, h3, c, np.abs(psi) ** 2)
+    np.testing.assert_allclose(mu, mu_exact, rtol=1e-9, atol=1e-9 * mu_exact[2])
+    k2 = oracle.krylov2(mu, c)
+    A = np.array([[mu[i + j + 1] for j in range(3)] for i in range(3)])
+    B = np.array([[mu[i + j] for j in range(3)] for i in range(3)])
+    ev = scipy.linalg.eigh(A, B, eigvals_only=True)
+    assert abs(k2["E"] - (c + ev[0])) < 1e-9 * abs(k2["E"])
+    Q, _ = np.linalg.qr(np.stack([psi, H @ psi, H @ (H @ psi)], 1))
+    rr = np.linalg.eigvalsh(Q.conj().T @ (H @ Q))[0]
+    assert abs(k2["E"] - rr) < 1e-8 * abs(rr)
+    E0 = spla.eigsh(H, k=1, which="SA")[0][0]
+    m4 = oracle.moments(h1, h2, np.abs(psi) ** 2)
+    E1 = oracle.lanczos_step(m4["m"])["E"]
+    assert E0 - 1e-9 <= k2["E"] <= E1 + 1e-9
+    x = k2["x"]
+    assert x[0] == 1.0
+    phi = vs[0] + x[1] * vs[1] + x[2] * vs[2]
+    hphi = H @ phi
+    pn = np.vdot(phi, phi).real
+    Ephi = np.vdot(phi, hphi).real / pn
+    assert abs(Ephi - k2["E"]) < 1e-9 * abs(Ephi)
+    var = np.vdot(hphi, hphi).real / pn - Ephi ** 2
+    assert abs(k2["var"] - var) < 1e-6 * abs(var) + 1e-12
+    # the shift does not change the step
+    mu2, _ = oracle.shifted_moments(h1, h2, h3, c + 0.37, np.abs(psi) ** 2)
+    assert abs(oracle.krylov2(mu2, c + 0.37)["E"] - k2["E"]) < 1e-8 * abs(k2["E"])
