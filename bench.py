@@ -59,10 +59,9 @@ WORKLOAD = "6x6 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=72), 288 ops + spin in
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
 BF16_PEAK_TFLOPS = 1900.3   # measured dense bf16 burst figure of the GB300s
 FLOPS_PER_ELEMENT = 28   # one connected factor p e^D + (1-p) e^-D and its running product
-# DRAM bytes (read + write) per E_loc launch of this workload: the ncu capture of
-# profiles/vmc_step_6x6.md measured 0.42 MB for 2048 samples; the
-# traffic grows with the samples, so a 16384-sample launch moves 8x that.
-K_RATIO_TRAFFIC = 8 * 0.418304e6
+# DRAM bytes (read + write) per E_loc launch of this workload from an ncu
+# capture of the current kernel (None until one is taken).
+K_RATIO_TRAFFIC = None
 
 
 LZ_L, LZ_M, LZ_SAMPLES, LZ_SUBSET = 8, 128, 4096, 912   # subset: 6 x 152 SMs
