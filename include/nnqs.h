@@ -165,6 +165,27 @@ int nnqs_local_energy(nnqs_model *model, const uint64_t *cfg, int64_t n, double 
 int nnqs_lanczos_moments(nnqs_model *model, const uint64_t *cfg, int64_t n, double *h1_out,
                          double *h2_out, double *moments_out, double *lanczos_out, void *stream);
 
+/* The p = 2 Lanczos step (Sec. 3.3: |Psi_2> = (1 + beta_1 H + beta_2 H^2)|psi0>).
+ * Per configuration
+ *   h3 = (H^3 psi)(s)/psi(s) = diag(s) h2(s) + sum_b (J_b/2) [psi(s^b)/psi(s)] h2(s^b)
+ * over the anti-aligned bonds b of s (h3_out: [n][2], may be NULL); over the n
+ * samples of |psi|^2 the FP64 moments about c = <Re h1>
+ *   mu_out[0..7] = {mu_0 = 1, mu_1, ..., mu_6, c},
+ *   mu_k = <psi|(H - c)^k|psi>/<psi|psi>  (from a_i = ((H - c)^i psi)/psi:
+ *   mu_{i+j} = <Re(conj(a_i) a_j)>),
+ * and the lowest eigenpair of the 3x3 Krylov pencil A_ij = mu_{i+j+1},
+ * B_ij = mu_{i+j} (i, j = 0..2):
+ *   out[0..4] = {E_p2, x0 = 1, x1, x2, var_p2},  Psi_2 = sum_i x_i (H - c)^i psi0.
+ * mu_out and out may be NULL.  Cost: one Lanczos-mode pass over every
+ * first-level neighbour (about 2N per sample), i.e. about 2N p = 1 steps.
+ * The neighbours' own amplitudes divide out of the formula, so a neighbour
+ * whose projected amplitude vanishes (possible only for characters other than
+ * +1, e.g. B1 or K != (0,0)) makes h3 undefined and raises NNQS_ERANGE in
+ * nnqs_status.  Needs workspace for n x 4N neighbour configurations;
+ * synchronises the stream once (to read the number of neighbours).  n >= 1. */
+int nnqs_lanczos2(nnqs_model *model, const uint64_t *cfg, int64_t n, double *h3_out, double *mu_out, double *out,
+                  void *stream);
+
 /* Energy variance of the p = 0 and p = 1 states and the variance
  * extrapolation (Sec. 3.3 Eq. 16; Sec. 4.3), in FP64 on the device.  The p = 1
  * state is phi = psi0 + alpha psi1, psi1 = (H - m1) psi0 / v, i.e.

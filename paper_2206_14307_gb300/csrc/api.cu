@@ -607,6 +607,71 @@ int nnqs_lanczos_moments_noalloc(nnqs_model *m, const uint64_t *cfg, int64_t n, 
     });
 }
 
+int nnqs_lanczos2(nnqs_model *m, const uint64_t *cfg, int64_t n, double *h3_out, double *mu_out, double *out,
+                  void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n < 1) return fail(NNQS_EINVAL, "n must be >= 1");
+    if (!cfg) return fail(NNQS_EINVAL, "cfg must be non-NULL");
+    const int64_t tmax = n * (int64_t)m->nbonds;  // at most one neighbour per bond
+    if (tmax > 0x7fffffffLL) return fail(NNQS_EINVAL, "too many neighbour configurations (n x 4N >= 2^31)");
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        // workspace: every piece 256-byte aligned, sized for the upper bound of neighbours
+        size_t at = 0;
+        auto take = [&](size_t bytes) { const size_t o = at; at += align256(bytes); return o; };
+        const size_t o_cnt = take(n * 8), o_off = take((n + 1) * 8);
+        const size_t o_h1 = take(n * 16), o_h2 = take(n * 16), o_h3 = take(n * 16), o_lp = take(n * 16);
+        const size_t o_part = take(64 * kMomentSums * 8), o_mom = take(8 * 8), o_part2 = take(kShiftBlocks * 8 * 8);
+        const size_t o_ncfg = take((size_t)tmax * m->nwords * 8), o_ncoef = take((size_t)tmax * 8);
+        const size_t o_lpn = take((size_t)tmax * 16), o_h1n = take((size_t)tmax * 16), o_h2n = take((size_t)tmax * 16);
+        int rc = ensure_ws(m, at);
+        if (rc) return rc;
+        char *ws = (char *)m->ws;
+        int64_t *cnt = (int64_t *)(ws + o_cnt), *off = (int64_t *)(ws + o_off);
+        double *h1 = (double *)(ws + o_h1), *h2 = (double *)(ws + o_h2), *lp = (double *)(ws + o_lp);
+        double *h3 = h3_out ? h3_out : (double *)(ws + o_h3);
+        double *part = (double *)(ws + o_part), *mom = (double *)(ws + o_mom), *part2 = (double *)(ws + o_part2);
+        uint64_t *ncfg = (uint64_t *)(ws + o_ncfg);
+        double *ncoef = (double *)(ws + o_ncoef), *lpn = (double *)(ws + o_lpn);
+        double *h1n = (double *)(ws + o_h1n), *h2n = (double *)(ws + o_h2n);
+        cudaError_t e = m->fp64 ? launch_expand_nb(view<double>(m), cfg, n, cnt, off, st)
+                                : launch_expand_nb(view<float>(m), cfg, n, cnt, off, st);
+        if (e != cudaSuccess) return cuda_fail(e, "neighbour count");
+        int64_t T = 0;
+        NNQS_CUDA(cudaMemcpyAsync(&T, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        NNQS_CUDA(cudaStreamSynchronize(st));
+        if (T < 0 || T > tmax) return fail(NNQS_ECUDA, "neighbour count %lld out of range", (long long)T);
+        auto log_psi = [&](const uint64_t *c, int64_t k, double *o) -> cudaError_t {
+            if (k == 0) return cudaSuccess;
+            if (m->fp64) return launch_log_psi(view<double>(m), c, k, o, m->nsm, st);
+            if (m->ns) return launch_log_psi_tc(view<float>(m), m->bimg, m->pinv, m->ns, c, k, o, m->nsm, st);
+            return launch_log_psi(view<float>(m), c, k, o, m->nsm, st);
+        };
+        auto ratio = [&](const uint64_t *c, int64_t k, double *a, double *b) -> cudaError_t {
+            if (k == 0) return cudaSuccess;
+            return m->fp64 ? launch_ratio(view<double>(m), c, k, 1, a, b, m->nsm, st)
+                           : launch_ratio(view<float>(m), c, k, 1, a, b, m->nsm, st);
+        };
+        e = m->fp64 ? launch_fill_nb(view<double>(m), cfg, n, off, ncfg, ncoef, st)
+                    : launch_fill_nb(view<float>(m), cfg, n, off, ncfg, ncoef, st);
+        if (e == cudaSuccess) e = log_psi(cfg, n, lp);
+        if (e == cudaSuccess) e = log_psi(ncfg, T, lpn);
+        if (e == cudaSuccess) e = ratio(cfg, n, h1, h2);
+        if (e == cudaSuccess) e = ratio(ncfg, T, h1n, h2n);
+        if (e == cudaSuccess)
+            e = m->fp64 ? launch_h3(view<double>(m), cfg, n, off, ncoef, lp, lpn, h2, h2n, h3, st)
+                        : launch_h3(view<float>(m), cfg, n, off, ncoef, lp, lpn, h2, h2n, h3, st);
+        if (e != cudaSuccess) return cuda_fail(e, "lanczos2 (h3)");
+        if (mu_out || out) {
+            e = launch_moments(h1, h2, n, part, 64, mom, nullptr, st);  // c = mom[1] = <Re h1>
+            if (e == cudaSuccess) e = launch_krylov2(h1, h2, h3, n, mom + 1, part2, kShiftBlocks, mu_out, out, st);
+            if (e != cudaSuccess) return cuda_fail(e, "lanczos2 (moments)");
+        }
+        return NNQS_OK;
+    });
+}
+
 int nnqs_lanczos_variance(const double *moments, const double *lanczos, double *out, void *stream)
 {
     if (!moments || !lanczos || !out) return fail(NNQS_EINVAL, "moments, lanczos and out must be non-NULL");

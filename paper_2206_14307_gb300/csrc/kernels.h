@@ -36,6 +36,21 @@ cudaError_t launch_structure_factor(const uint64_t *cfg, int64_t n, int L, int n
                                     double *partial, int grid, double *sq_out, cudaStream_t st);
 cudaError_t launch_lanczos_variance(const double *moments, const double *lanczos, double *out, cudaStream_t st);
 
+// p = 2 Lanczos step: first-level neighbours, h3, moments about c and the 3x3 pencil
+constexpr int kShiftBlocks = 64;
+template <typename T>
+cudaError_t launch_expand_nb(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int64_t *cnt, int64_t *off,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_fill_nb(const DevModel<T> &md, const uint64_t *cfg, int64_t n, const int64_t *off,
+                           uint64_t *nb_cfg, double *nb_coef, cudaStream_t st);
+template <typename T>
+cudaError_t launch_h3(const DevModel<T> &md, const uint64_t *cfg, int64_t n, const int64_t *off,
+                      const double *nb_coef, const double *lp, const double *lpn, const double *h2,
+                      const double *h2n, double *h3, cudaStream_t st);
+cudaError_t launch_krylov2(const double *h1, const double *h2, const double *h3, int64_t n, const double *c_ptr,
+                           double *partial, int nb, double *mu_out, double *out, cudaStream_t st);
+
 // Mixed batch (Lanczos mode): one persistent launch over (instance, sample)
 // items; each instance runs with its own tile shape (GL lanes per row, MPL
 // hidden units per lane).

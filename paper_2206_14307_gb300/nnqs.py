@@ -31,6 +31,7 @@ ABI_FUNCTIONS = (
     "nnqs_num_tile_shapes", "nnqs_tile_shape", "nnqs_batch_create", "nnqs_batch_destroy", "nnqs_batch_size",
     "nnqs_batch_model", "nnqs_batch_get_shape", "nnqs_batch_set_shape", "nnqs_batch_autotune",
     "nnqs_batch_lanczos", "nnqs_batch_status", "nnqs_lanczos_variance", "nnqs_structure_factor",
+    "nnqs_lanczos2",
 )
 NOALLOC_MAX_SAMPLES = 65536
 
@@ -81,6 +82,7 @@ def lib():
             "nnqs_lanczos_moments_noalloc": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_last_error": ([], ctypes.c_char_p),
             "nnqs_lanczos_variance": ([P, P, P, P], ctypes.c_int),
+            "nnqs_lanczos2": ([P, P, i64, P, P, P, P], ctypes.c_int),
             "nnqs_structure_factor": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_num_tile_shapes": ([], i32),
             "nnqs_tile_shape": ([i32, P, P], ctypes.c_int),
@@ -151,6 +153,10 @@ def nnqs_status(h, stream=0): return _check(lib().nnqs_status(h, stream))
 
 def nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream=0):
     return _check(lib().nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream))
+
+
+def nnqs_lanczos2(h, cfg, n, h3, mu, out, stream=0):
+    return _check(lib().nnqs_lanczos2(h, cfg, n, h3, mu, out, stream))
 
 
 def nnqs_lanczos_variance(moments, lanczos, out, stream=0):
@@ -314,6 +320,15 @@ class Model:
         nnqs_sr_solve(self.h, O.data_ptr(), _ptr(weights), n, F.data_ptr(), float(lam), float(dtau), int(max_iter),
                       float(tol), delta.data_ptr(), info.data_ptr(), _ptr(params_inout), _stream())
         return delta, info
+
+    def lanczos2(self, cfg, h3=None, mu=None, out=None):
+        """p = 2 step: (h3 [n][2], mu [8] = mu_0..mu_6 and c, out [5] = E_p2, x0..x2, var_p2)."""
+        n = cfg.shape[0]
+        h3 = self._out(n, 2) if h3 is None else h3
+        mu = self._out(8) if mu is None else mu
+        out = self._out(5) if out is None else out
+        nnqs_lanczos2(self.h, cfg.data_ptr(), n, h3.data_ptr(), mu.data_ptr(), out.data_ptr(), _stream())
+        return h3, mu, out
 
     def structure_factor(self, cfg, weights=None, out=None):
         """S(q) [N] for q = 2 pi (qx, qy)/L at index qx + L qy."""
