@@ -420,12 +420,13 @@ def main():
     ap.add_argument("--lanczos-steps", type=int, default=2)
     ap.add_argument("--mixed", action="store_true", help="add the 64-instance mixed batch (about 80 s)")
     ap.add_argument("--small", action="store_true",
-                    help="128 chains instead of 1024 (for profiler captures; not a bench line)")
+                    help="128 chains and a 512-sample Lanczos leg (for profiler captures; not a bench line)")
     args = ap.parse_args()
     if args.small:
-        global N_CHAINS, N_SAMPLES
+        global N_CHAINS, N_SAMPLES, LZ_SAMPLES, LZ_SUBSET
         N_CHAINS = 128
         N_SAMPLES = N_CHAINS * N_PER_CHAIN
+        LZ_SAMPLES, LZ_SUBSET = 512, 152
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -29,6 +29,17 @@ template <typename T> struct Entry2 {
 };
 enum { kOneBond = 0, kTwoBonds = 1, kSitePair = 2 };
 
+// E_loc mode of the narrow FP32 variants (GL = 8, M <= 72) reads the per-site
+// tables exp(-+4W) ([K][2][N][Mp], small enough to stay in L1) and forms
+// 1 + T = e^{-4 s_u W_u} e^{+4 s_u W_v} per element, instead of the per-bond
+// tables T ([K][2][4N][Mp], four times larger); the wider variants keep the
+// per-bond tables (the second table stream costs them registers), and so does
+// FP64, where the extra complex multiply costs more than the cache misses.
+template <typename T, int GL, int MPL> __host__ __device__ constexpr bool eloc_site_pairs()
+{
+    return sizeof(T) == 4 && GL == 8 && MPL <= 9;
+}
+
 __device__ __forceinline__ uint32_t ecode(int type, int i0, int i1)
 {
     return (uint32_t)i0 | ((uint32_t)i1 << 15) | ((uint32_t)type << 30);
@@ -41,7 +52,7 @@ __device__ __forceinline__ uint32_t ecode(int type, int i0, int i1)
 //     slot 1 + b2 -> second-level configuration after exchanging b2 in s^{b1}:
 //       one shared site (b2 anti-aligned in s^{b1}) -> pair of flipped sites,
 //       disjoint, anti-aligned, b2 > b1             -> both bonds, counted twice.
-template <typename T>
+template <bool SITE, typename T>
 __device__ __forceinline__ bool candidate2(const DevModel<T> &md, int mode, int q, const int8_t *s8,
                                            const int16_t *aa, T diag, Entry2<T> &e)
 {
@@ -49,7 +60,8 @@ __device__ __forceinline__ bool candidate2(const DevModel<T> &md, int mode, int 
     if (mode == 0) {
         const int i = md.bond_i[q], j = md.bond_j[q];
         if (s8[i] == s8[j]) return false;
-        e.code = ecode(kOneBond, q, s8[i] > 0);
+        // exchanging an anti-aligned bond flips its two sites
+        e.code = SITE ? ecode(kSitePair, i, j) : ecode(kOneBond, q, s8[i] > 0);
         e.c1 = T(0.5) * bondJ(md, q);
         e.c2 = T(0);
         return true;
@@ -163,13 +175,25 @@ __device__ __forceinline__ Dec<T> decode(const DevModel<T> &md, uint32_t code, i
 // prod over the lane's hidden units m = gl + GL j of (1 + p_m T_m) for one
 // entry and one sign.  The tables are padded to GL * MPL with neutral entries
 // (and p_m = 0 past M), so no bound check is needed.
-template <typename T, int GL, int MPL, bool ONLY1>
+template <typename T, int GL, int MPL, bool ONLY1, bool ONLYSITE = false>
 __device__ __forceinline__ cx<T> entry_partial(const DevModel<T> &md, const Dec<T> &d, int sg, const cx<T> (&p)[MPL],
                                                int gl)
 {
     const int o0 = (sg ? d.o0 + d.d0 : d.o0) + gl;
     const int o1 = (sg ? d.o1 + d.d1 : d.o1) + gl;
     cx<T> pr{T(1), T(0)};
+    if constexpr (ONLYSITE) {
+        const cx<T> *__restrict__ t0p = md.S4 + o0;
+        const cx<T> *__restrict__ t1p = md.S4 + o1;
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) {
+            const cx<T> x = cmul(t0p[GL * j], t1p[GL * j]);
+            const cx<T> t{x.x - T(1), x.y};
+            const cx<T> f{T(1) + p[j].x * t.x - p[j].y * t.y, p[j].x * t.y + p[j].y * t.x};
+            pr = cmul(pr, f);
+        }
+        return pr;
+    }
     if (ONLY1 || d.type == kOneBond) {
         const cx<T> *__restrict__ tb = md.Tb + o0;
 #pragma unroll
@@ -292,7 +316,7 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
             if (cur >= ncand || S.n_ent >= chunk) break;
             const int q = cur + threadIdx.x;
             Entry2<T> e;
-            const bool valid = q < ncand && candidate2(md, mode, q, S.s8, S.aa, S.diag_sh, e);
+            const bool valid = q < ncand && candidate2<eloc_site_pairs<T, GL, MPL>()>(md, mode, q, S.s8, S.aa, S.diag_sh, e);
             const unsigned bm = __ballot_sync(0xffffffffu, valid);
             if (lane == 0) S.wcount[warp] = __popc(bm);
             if (threadIdx.x == 0) S.first_over = INT_MAX;
@@ -408,7 +432,7 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
                             cx<T> pr{T(1), T(0)};
                             if (e < ne) {
                                 const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, S.s8);
-                                pr = entry_partial<T, GL, MPL, MODE == 0>(md, d, sg, p[sg], gl);
+                                pr = entry_partial<T, GL, MPL, MODE == 0 && !eloc_site_pairs<T, GL, MPL>(), MODE == 0 && eloc_site_pairs<T, GL, MPL>()>(md, d, sg, p[sg], gl);
                             }
                             T sx, sy;
                             int ex;
@@ -468,7 +492,7 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
                             cx<T> pr{T(1), T(0)};
                             if (e < ne) {
                                 const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, S.s8);
-                                pr = entry_partial<T, GL, MPL, MODE == 0>(md, d, sg, p[sg], gl);
+                                pr = entry_partial<T, GL, MPL, MODE == 0 && !eloc_site_pairs<T, GL, MPL>(), MODE == 0 && eloc_site_pairs<T, GL, MPL>()>(md, d, sg, p[sg], gl);
                             }
                             T sx, sy;
                             int ex;
@@ -584,9 +608,9 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
 template <typename T, int GL, int MPL, int MODE> constexpr int eloc_min_blocks()
 {
     if (sizeof(T) != 4) return 1;
-    if (GL == 8) return (MPL <= 4 || MODE == 0) ? 3 : 1;
-    if (GL == 16) return MPL == 8 ? 3 : 1;
-    return MPL == 8 ? 3 : 1;
+    if (GL == 8) return (MPL <= 4 || MODE == 0) ? 3 : 2;
+    if (GL == 16) return MPL == 8 ? 3 : 2;
+    return MPL == 8 ? 3 : 2;
 }
 
 template <typename T, int GL, int MPL, int MODE>

@@ -25,6 +25,23 @@ constexpr int kSThreads = 32 * kSWarps;
 // Layout of one chain's cache: [p buffer 0][terms 0][p buffer 1][terms 1],
 // every segment padded to 256 bytes so that each starts aligned.
 __host__ __device__ __forceinline__ size_t pad256(size_t b) { return (b + 255) & ~(size_t)255; }
+// Complex division for the speculative cache update, where the divisor
+// f = 1 + p (e^{2 Delta} - 1) stays near 1: the reciprocal of |f|^2 from the
+// hardware approximation refined by one Newton-Raphson step (r' = r + r(1 - x r)),
+// within an ulp of the correctly rounded one.
+__device__ __forceinline__ float rcp_nr(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ double rcp_nr(double x) { return 1.0 / x; }
+template <typename T> __device__ __forceinline__ cx<T> cdiv_upd(cx<T> a, cx<T> b)
+{
+    const T d = rcp_nr(b.x * b.x + b.y * b.y);
+    return cx<T>{(a.x * b.x + a.y * b.y) * d, (a.y * b.x - a.x * b.y) * d};
+}
+
 template <typename T> __host__ __device__ size_t seg_p(int K, int G, int nsign, int M)
 {
     return pad256((size_t)K * G * nsign * M * sizeof(cx<T>));
@@ -232,7 +249,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
                                 const cx<T> p = pv_[jj];
                                 const cx<T> f{T(1) + p.x * tt.x - p.y * tt.y, p.x * tt.y + p.y * tt.x};
                                 prod = cmul(prod, f);
-                                if (active) pr_out[m] = cdiv(cmul(p, e2), f);
+                                if (active) pr_out[m] = cdiv_upd(cmul(p, e2), f);
                             }
                         }
                     }
