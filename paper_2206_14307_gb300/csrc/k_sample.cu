@@ -98,7 +98,6 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
     const int slot = warp * NG + grp, nslots = kSWarps * NG;
     const size_t per_chain = chain_stride<T>(md.K, md.G, md.nsign, M);
     const size_t pbytes = seg_p<T>(md.K, md.G, md.nsign, M), tbytes = seg_t<T>(md.K, md.G, md.nsign);
-    (void)nrs;
 
     for (int chain = blockIdx.x; chain < n_chains; chain += gridDim.x) {
         unsigned char *base = cache + per_chain * chain;
@@ -213,17 +212,20 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
             sc<T> *T1 = cb ? tc0 : tc1;
             // ---- ratio of the proposal, and the speculative update ----
             sc<T> so{T(0), T(0), 0}, sn{T(0), T(0), 0};
-            for (int rbase = 0; rbase < rows; rbase += nslots) {
-                const int row0 = rbase + slot;
-                const bool active = row0 < rows;
-                const int row = active ? row0 : 0;
+            // one (row, sign) pair per group and iteration: K |G| n_sign pairs
+            // divide the groups evenly where K |G| alone does not
+            for (int tbase = 0; tbase < nrs; tbase += nslots) {
+                const int t0 = tbase + slot;
+                const bool active = t0 < nrs;
+                const int t = active ? t0 : 0;
+                const int row = md.nsign == 2 ? t >> 1 : t;
+                const int sg = t - row * md.nsign;
                 const int r = row / md.G, g = row - r * md.G;
                 const int ku = md.perm[(size_t)g * N + iu], kd = md.perm[(size_t)g * N + id];
                 const size_t rs = (size_t)r * 2 * N * md.Mp;
                 const sc<T> *ESr = md.ES + (size_t)r * 2 * N;
-                for (int sg = 0; sg < md.nsign; ++sg) {
+                {
                     // site u holds +1: sigma = sign
-                    const int t = row * md.nsign + sg;
                     const cx<T> *Su = md.S4 + rs + ((size_t)sg * N + ku) * md.Mp;         // exp(-4 sigma W_u)
                     const cx<T> *Sd = md.S4 + rs + ((size_t)(sg ^ 1) * N + kd) * md.Mp;   // exp(+4 sigma W_d)
                     const cx<T> *__restrict__ pr_in = P0 + (size_t)t * M;
