@@ -175,9 +175,22 @@ __device__ __forceinline__ Dec<T> decode(const DevModel<T> &md, uint32_t code, i
 // prod over the lane's hidden units m = gl + GL j of (1 + p_m T_m) for one
 // entry and one sign.  The tables are padded to GL * MPL with neutral entries
 // (and p_m = 0 past M), so no bound check is needed.
+// Per-lane state of the Lanczos mode for pairs of disjoint exchanged bonds
+// (b1, b2), which the candidate order keeps consecutive for a fixed b1: after
+// the first exchange p_m becomes p'_m = p_m (1 + T1_m) / (1 + p_m T1_m) (the
+// p of the configuration with b1 exchanged), so that
+//   prod_m (1 + p_m T12_m) = prod_m (1 + p_m T1_m) * prod_m (1 + p'_m T2_m),
+// one table row per element instead of two.  key identifies (T1 row, sign)
+// within one row (r, g) of the projected sum; -1 = empty.
+template <typename T, int MPL> struct PairCache {
+    int key;
+    cx<T> q1;        // prod over the lane's units of (1 + p T1)
+    cx<T> pp[MPL];   // p' of the lane's units
+};
+
 template <typename T, int GL, int MPL, bool ONLY1, bool ONLYSITE = false>
 __device__ __forceinline__ cx<T> entry_partial(const DevModel<T> &md, const Dec<T> &d, int sg, const cx<T> (&p)[MPL],
-                                               int gl)
+                                               int gl, PairCache<T, MPL> *pc = nullptr)
 {
     const int o0 = (sg ? d.o0 + d.d0 : d.o0) + gl;
     const int o1 = (sg ? d.o1 + d.d1 : d.o1) + gl;
@@ -203,6 +216,32 @@ __device__ __forceinline__ cx<T> entry_partial(const DevModel<T> &md, const Dec<
             pr = cmul(pr, f);
         }
     } else if constexpr (!ONLY1) {
+        if (pc && d.type == kTwoBonds) {
+            const int key = 2 * o0 + sg;
+            if (key != pc->key) {
+                pc->key = key;
+                const cx<T> *__restrict__ t1p = md.Tb + o0;
+                cx<T> q{T(1), T(0)};
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    const cx<T> t = t1p[GL * j];
+                    const cx<T> f{T(1) + p[j].x * t.x - p[j].y * t.y, p[j].x * t.y + p[j].y * t.x};
+                    q = cmul(q, f);
+                    pc->pp[j] = cdiv(cmul(p[j], cx<T>{T(1) + t.x, t.y}), f);
+                }
+                pc->q1 = q;
+            }
+            const cx<T> *__restrict__ t2p = md.Tb + o1;
+            pr = pc->q1;
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                const cx<T> t = t2p[GL * j];
+                const cx<T> q = pc->pp[j];
+                const cx<T> f{T(1) + q.x * t.x - q.y * t.y, q.x * t.y + q.y * t.x};
+                pr = cmul(pr, f);
+            }
+            return pr;
+        }
         const cx<T> *__restrict__ tab = d.type == kTwoBonds ? md.Tb : md.S4;
         const cx<T> *__restrict__ t0p = tab + o0;
         const cx<T> *__restrict__ t1p = tab + o1;
@@ -347,6 +386,8 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
 
         sc<T> a0{T(0), T(0), 0};
         for (int rbase = 0; rbase < rows; rbase += nslots) {
+            PairCache<T, MPL> pcache;
+            pcache.key = -1;
             const int row = rbase + slot;
             const bool active = row < rows;
             const int r = active ? row / md.G : 0, g = active ? row - (row / md.G) * md.G : 0;
@@ -432,7 +473,7 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
                             cx<T> pr{T(1), T(0)};
                             if (e < ne) {
                                 const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, S.s8);
-                                pr = entry_partial<T, GL, MPL, MODE == 0 && !eloc_site_pairs<T, GL, MPL>(), MODE == 0 && eloc_site_pairs<T, GL, MPL>()>(md, d, sg, p[sg], gl);
+                                pr = entry_partial<T, GL, MPL, MODE == 0 && !eloc_site_pairs<T, GL, MPL>(), MODE == 0 && eloc_site_pairs<T, GL, MPL>()>(md, d, sg, p[sg], gl, (MODE == 1 && MPL <= 13) ? &pcache : nullptr);
                             }
                             T sx, sy;
                             int ex;
@@ -492,7 +533,7 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
                             cx<T> pr{T(1), T(0)};
                             if (e < ne) {
                                 const Dec<T> d = decode<T, false>(md, ent[e].code, r, g, S.s8);
-                                pr = entry_partial<T, GL, MPL, MODE == 0 && !eloc_site_pairs<T, GL, MPL>(), MODE == 0 && eloc_site_pairs<T, GL, MPL>()>(md, d, sg, p[sg], gl);
+                                pr = entry_partial<T, GL, MPL, MODE == 0 && !eloc_site_pairs<T, GL, MPL>(), MODE == 0 && eloc_site_pairs<T, GL, MPL>()>(md, d, sg, p[sg], gl, (MODE == 1 && MPL <= 13) ? &pcache : nullptr);
                             }
                             T sx, sy;
                             int ex;
@@ -604,12 +645,13 @@ __device__ __forceinline__ void eloc_sample(const DevModel<T> &md, const uint64_
 }
 
 // CTAs per SM the register budget is sized for: three (80 registers) where
-// the FP32 variant needs no spill at that budget, else what the compiler picks.
+// the FP32 variant needs no spill at that budget, else two (128 registers);
+// FP64 is left to the compiler.
 template <typename T, int GL, int MPL, int MODE> constexpr int eloc_min_blocks()
 {
     if (sizeof(T) != 4) return 1;
-    if (GL == 8) return (MPL <= 4 || MODE == 0) ? 3 : 2;
-    if (GL == 16) return MPL == 8 ? 3 : 2;
+    if (MODE == 1) return (GL == 8 && MPL <= 4) ? 3 : 2;   // the pair cache needs registers
+    if (GL == 8) return 3;
     return MPL == 8 ? 3 : 2;
 }
 
