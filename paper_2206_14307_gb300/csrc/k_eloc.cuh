@@ -675,10 +675,11 @@ template <typename T, int GL> size_t eloc_smem(int chunk)
 }
 
 // Entries gathered per pass in the Lanczos mode: small enough that the
-// shared memory of three CTAs fits an SM where the registers allow three.
+// shared memory of three CTAs fits an SM where the registers allow three, and
+// at two CTAs small enough to leave L1 room for the per-bond table rows.
 template <typename T, int GL, int MPL> constexpr int eloc_lanczos_chunk()
 {
-    return eloc_min_blocks<T, GL, MPL, 1>() < 3 ? 512 : (GL == 16 ? 160 : 384);
+    return eloc_min_blocks<T, GL, MPL, 1>() < 3 ? 256 : (GL == 16 ? 160 : 384);
 }
 
 template <typename T, int GL, int MPL, int MODE>
