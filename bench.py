@@ -59,9 +59,11 @@ WORKLOAD = "6x6 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=72), 288 ops + spin in
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
 BF16_PEAK_TFLOPS = 1900.3   # measured dense bf16 burst figure of the GB300s
 FLOPS_PER_ELEMENT = 28   # one connected factor p e^D + (1-p) e^-D and its running product
-# DRAM bytes (read + write) per E_loc launch of this workload from an ncu
-# capture of the current kernel (None until one is taken).
-K_RATIO_TRAFFIC = None
+# DRAM bytes (read + write) per launch, from the ncu captures of the current
+# kernels on the 2048-sample (E_loc) and 512-sample (Lanczos) cases; the
+# traffic grows with the samples, so the full launches move 8x that.
+K_RATIO_TRAFFIC = 8 * 0.217856e6
+K_LANCZOS_TRAFFIC = 8 * 1.236224e6
 
 
 LZ_L, LZ_M, LZ_SAMPLES, LZ_SUBSET = 8, 128, 4096, 912   # subset: 6 x 152 SMs
@@ -501,7 +503,7 @@ def main():
             "flip_sets_per_sample": lz["entries"] / lz["samples"],
             "roofline": {"kernel": "k_eloc Lanczos mode (all flip-set kinds)", "bound": "alu",
                          "achieved": lz_ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": lz_ach / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": lz_ach / FP32_PEAK_TFLOPS, "traffic": K_LANCZOS_TRAFFIC,
                          "work": f"{lz['entries']} flip sets x |G|={lz['G']} x M={Ml} x {FLOPS_PER_ELEMENT} flop"},
         }
         if "ms_sub64" in lz:
