@@ -5,7 +5,7 @@ import numpy as np
 import oracle
 from paper_2206_14307_gb300 import synth
 
-# BASELINE-style workloads (shapes only; values are seeded synthetic)
+# The paper-sized workloads used by the tests (shapes only; values are seeded synthetic)
 CONFIG_4x4 = dict(L=4, J2=0.5, K=1, alpha=1, proj=False, spin_inv=0)
 CONFIG_6x6 = dict(L=6, J2=0.5, K=1, alpha=2, proj=True, spin_inv=1)
 CONFIG_10x10 = dict(L=10, J2=0.5, K=4, alpha=4, proj=True, spin_inv=0)
