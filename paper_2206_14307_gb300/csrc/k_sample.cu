@@ -223,7 +223,6 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
                 const int r = row / md.G, g = row - r * md.G;
                 const int ku = md.perm[(size_t)g * N + iu], kd = md.perm[(size_t)g * N + id];
                 const size_t rs = (size_t)r * 2 * N * md.Mp;
-                const sc<T> *ESr = md.ES + (size_t)r * 2 * N;
                 {
                     // site u holds +1: sigma = sign
                     const cx<T> *Su = md.S4 + rs + ((size_t)sg * N + ku) * md.Mp;         // exp(-4 sigma W_u)
@@ -263,16 +262,25 @@ __global__ void __launch_bounds__(kSThreads, 1) k_sample(DevModel<T> md, uint64_
                         const sc<T> w{shfl_x(pv.x, o), shfl_x(pv.y, o), __shfl_xor_sync(0xffffffffu, pv.e, o)};
                         pv = sc_mul(pv, w);
                     }
-                    if (gl == 0 && active) {
-                        // prefactor exp(sigma (Cs_u - Cs_d)), sigma = sign
-                        const sc<T> pref = sc_mul(ESr[(size_t)sg * N + ku], ESr[(size_t)(sg ^ 1) * N + kd]);
-                        const sc<T> term = T0[t];
-                        const sc<T> tn = sc_mul(sc_mul(term, pv), pref);
-                        T1[t] = tn;
-                        so = sc_add(so, term);
-                        sn = sc_add(sn, tn);
-                    }
+                    // the pair's product over m, staged in its next-term slot
+                    if (gl == 0 && active) T1[t] = pv;
                 }
+            }
+            __syncthreads();
+            // every thread finishes pairs: prefactor exp(sigma (Cs_u - Cs_d)),
+            // sigma = sign, the new term, and the old and new sums
+            for (int t = threadIdx.x; t < nrs; t += blockDim.x) {
+                const int row = md.nsign == 2 ? t >> 1 : t;
+                const int sg = t - row * md.nsign;
+                const int r = row / md.G, g = row - r * md.G;
+                const int ku = md.perm[(size_t)g * N + iu], kd = md.perm[(size_t)g * N + id];
+                const sc<T> *ESr = md.ES + (size_t)r * 2 * N;
+                const sc<T> pref = sc_mul(ESr[(size_t)sg * N + ku], ESr[(size_t)(sg ^ 1) * N + kd]);
+                const sc<T> term = T0[t];
+                const sc<T> tn = sc_mul(sc_mul(term, T1[t]), pref);
+                T1[t] = tn;
+                so = sc_add(so, term);
+                sn = sc_add(sn, tn);
             }
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
