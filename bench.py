@@ -25,7 +25,10 @@ samples; nnqs_lanczos_moments gives h1 = (H psi)/psi, h2 = (H^2 psi)/psi, the
 FP64 moments <H^n> (n <= 3) and E_p1.  Lanczos E_loc samples/s is timed on
 the full set in the FP32 engine, and on a common 512-sample subset in both
 the FP32 and the plain FP64 GPU forms for the speedup (912 = 6 x 152
-samples, whole waves of resident CTAs in both forms).  `--mixed` adds the
+samples, whole waves of resident CTAs in both forms).  A third leg
+times fresh amplitudes of the 10x10 configuration (K = 4, M = 400, |G| = 800,
+8192 configurations), where the theta GEMM is the dominant work (512 MFLOP
+per amplitude): tcgen05 BF16X2 against the FP32 SIMT form.  `--mixed` adds the
 64-instance mixed batch (one persistent graph-captured launch; about 80 s a
 call, so not in the default run).
 
@@ -260,6 +263,8 @@ def gpu_arm(args, rank, world):
     m32.close()
     if not args.no_lanczos:
         res["lanczos"] = lanczos_leg(args, rank, flush)
+    if not args.no_tc10:
+        res["tc10"] = tc10_leg(flush, min(args.steps, 5))
     if args.mixed:
         res["mixed"] = mixed_leg(flush)
     return res
@@ -322,6 +327,28 @@ def lanczos_leg(args, rank, flush):
         out["ms_sub64"] = _event_ms(small(m64), flush, 1)
         m64.close()
     return out
+
+
+def tc10_leg(flush, steps):
+    """Fresh log psi of 8192 configurations of the 10x10 configuration on the
+    tensor cores (BF16X2) and in the FP32 SIMT form."""
+    import torch
+    from paper_2206_14307_gb300 import nnqs, synth
+    L10, N10, M10, K10 = 10, 100, 400, 4
+    p = synth.random_params(N10, M10, K10, std=PARAM_STD, seed=PARAM_SEED, logc_std=0.2)
+    cfg = nnqs.cfg_tensor(synth.pack(synth.random_sz0(N10, 8192, seed=21)))
+    out = torch.empty(8192, 2, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, prec in (("bf16x2", nnqs.BF16X2), ("fp32", nnqs.FP32)):
+        m = nnqs.Model(L10, J1, J2, K=K10, M=M10, proj_t=True, proj_p=True, spin_inv=0, use_bias=True, precision=prec)
+        m.set_params(p)
+        run = lambda: m.log_psi(cfg, out=out)
+        run()
+        res[name] = _event_ms(run, flush, max(1, steps))
+        res["G"] = m.G
+        m.status()
+        m.close()
+    return res
 
 
 def mixed_leg(flush):
@@ -420,7 +447,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the 8x8 Lanczos leg")
     ap.add_argument("--lanczos-steps", type=int, default=2)
-    ap.add_argument("--mixed", action="store_true", help="add the 64-instance mixed batch (about 80 s)")
+    ap.add_argument("--no-tc10", action="store_true", help="skip the 10x10 fresh-amplitude leg")
+    ap.add_argument("--mixed", action="store_true", help="add the 64-instance mixed batch (about 60 s)")
     ap.add_argument("--small", action="store_true",
                     help="128 chains and a 512-sample Lanczos leg (for profiler captures; not a bench line)")
     args = ap.parse_args()
@@ -511,6 +539,18 @@ def main():
                                            "subset": LZ_SUBSET}
             line["lanczos"]["fp32_same_subset"] = LZ_SUBSET / (lz["ms_sub32"] / 1e3)
             line["lanczos"]["speedup_vs_fp64_gpu"] = lz["ms_sub64"] / lz["ms_sub32"]
+    if "tc10" in res:
+        t = res["tc10"]
+        flop = 4.0 * 4 * t["G"] * 400 * 100 * 8192   # 4 K |G| M N per amplitude
+        ach = flop / (t["bf16x2"] / 1e3) / 1e12
+        line["theta_gemm_10x10"] = {
+            "workload": "10x10 J1-J2, K=4 complex RBMs alpha=4 (M=400), 800 ops; fresh log psi of 8192 configurations",
+            "kernel": "k_logpsi_tc (4 hidden-unit tiles of 104)", "bound": "tensor",
+            "fresh_amplitudes_per_s": 8192 / (t["bf16x2"] / 1e3), "ms": t["bf16x2"],
+            "achieved": ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / BF16_PEAK_TFLOPS,
+            "peak_source": "MEASURED bf16 burst (of measured)",
+            "fp32_simt": {"fresh_amplitudes_per_s": 8192 / (t["fp32"] / 1e3), "ms": t["fp32"]},
+            "speedup_vs_fp32_simt": t["fp32"] / t["bf16x2"]}
     if "mixed" in res:
         mx = res["mixed"]
         line["mixed_batch"] = {"workload": "64 instances (Philox seed 5): L in {4,6,8,10}, J2/J1 in [0,0.7], "

@@ -10,7 +10,10 @@
 // relative per weight for two terms, 2^-25 for three).  A is built by the
 // threads in shared memory in the no-swizzle K-major core-matrix layout; B's
 // shared-memory image is laid out on the device once per parameter set and
-// brought in with a bulk (TMA) copy; the 128 x 2*M8 accumulator lives in TMEM.
+// brought in with a bulk (TMA) copy; the 128 x 2*MT accumulator lives in TMEM.
+// Hidden units are taken MT at a time (one tile when M <= 128; otherwise
+// ceil(M/128) tiles, each with its own B image, copied per 128-row tile): the
+// epilogue multiplies each tile's factors into the row's running products.
 // The epilogue reads each row from TMEM, forms prod_m 2cosh(b_m +- theta'_m)
 // as a scaled complex number, multiplies the leading factor
 // c_r chi(g) chi_P e^{+-a.t} and sums the rows of every sample (segmented
@@ -29,8 +32,9 @@ namespace nnqs {
 
 struct TcShape {
     int N, M, M8, NS, KD, NC, G, K, S, ntiles, nsign;
+    int MT, nmt;                 // hidden units per tile (multiple of 8), tiles; NC = 2 MT columns per tile
     uint32_t a_bytes, b_bytes;   // allocated (with margin) shared bytes of A and B
-    uint32_t b_img_bytes;        // bytes of one B image
+    uint32_t b_img_bytes;        // bytes of one B image (one tile of one RBM)
 };
 
 __host__ __device__ inline int gcd_i(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
@@ -40,7 +44,9 @@ TcShape tc_shape(int N, int M, int G, int K, int nsign, int NS)
     TcShape s;
     s.N = N; s.M = M; s.M8 = (M + 7) / 8 * 8; s.NS = NS;
     s.KD = (NS * N + 15) / 16 * 16;
-    s.NC = 2 * s.M8;
+    s.nmt = (s.M8 + 127) / 128;
+    s.MT = ((s.M8 + s.nmt - 1) / s.nmt + 7) / 8 * 8;
+    s.NC = 2 * s.MT;
     s.G = G; s.K = K; s.nsign = nsign;
     s.S = 128 / gcd_i(G, 128);
     s.ntiles = s.S * G / 128;
@@ -67,21 +73,24 @@ __host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int KD)
 }
 
 // ---------------------------------------------------------------------------
-// B images: for every RBM r, NC rows (Re W_m for n < M8, Im W_m after) x KD
-// columns (NS bf16 terms of W_m,j), zero-padded, in the core layout.
+// B images: for every RBM r and hidden-unit tile t, NC = 2 MT rows (Re W_m
+// for n < MT, Im W_m after, m = t MT + n mod MT) x KD columns (NS bf16 terms
+// of W_m,j), zero-padded (m >= M), in the core layout.
 // ---------------------------------------------------------------------------
-__global__ void k_bimg(const double *__restrict__ par, int N, int M, int K, int M8, int NS, int KD,
+__global__ void k_bimg(const double *__restrict__ par, int N, int M, int K, int MT, int nmt, int NS, int KD,
                        uint16_t *__restrict__ img)
 {
-    const int NC = 2 * M8;
+    const int NC = 2 * MT;
     const int64_t P1 = 1 + N + M + (int64_t)M * N;
     const int64_t per = (int64_t)NC * KD;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < per * K; q += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(q / per);
-        const int64_t rem = q - r * per;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < per * K * nmt;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int rt = (int)(q / per);           // r * nmt + t
+        const int r = rt / nmt, t = rt - r * nmt;
+        const int64_t rem = q - rt * per;
         const int n = (int)(rem / KD), k = (int)(rem - (int64_t)n * KD);
-        const int m = n < M8 ? n : n - M8;
-        const int part = n < M8 ? 0 : 1;
+        const int m = t * MT + (n < MT ? n : n - MT);
+        const int part = n < MT ? 0 : 1;
         const int split = k / N, j = k - split * N;
         float v = 0.f;
         if (m < M && split < NS) {
@@ -89,14 +98,14 @@ __global__ void k_bimg(const double *__restrict__ par, int N, int M, int K, int 
             // successive bf16 terms of w
             double rest = w;
             float term = 0.f;
-            for (int t = 0; t <= split; ++t) {
+            for (int u = 0; u <= split; ++u) {
                 term = __bfloat162float(__float2bfloat16_rn((float)rest));
                 rest -= (double)term;
             }
             v = term;
         }
         const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        img[(size_t)r * (per) + core_off(n, k, KD) / 2] = *reinterpret_cast<const uint16_t *>(&b);
+        img[(size_t)rt * per + core_off(n, k, KD) / 2] = *reinterpret_cast<const uint16_t *>(&b);
     }
 }
 
@@ -108,7 +117,7 @@ constexpr uint32_t kTmemCols = 256;
 
 struct TcArgs {
     TcShape sh;
-    const uint16_t *bimg;     // [K][NC x KD] core-layout images
+    const uint16_t *bimg;     // [K][nmt][NC x KD] core-layout images
     const uint8_t *pinv;      // [G][N] inverse permutations: (T_g s)_j = s_{pinv[g][j]}
 };
 
@@ -131,8 +140,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;
-    const int N = sh.N, M = sh.M, M8 = sh.M8, KD = sh.KD, G = sh.G;
-    const int nchunk = M8 / 8, c0 = (nchunk + 1) / 2;
+    const int N = sh.N, M = sh.M, MT = sh.MT, KD = sh.KD, G = sh.G;
+    const int nchunk = MT / 8, c0 = (nchunk + 1) / 2;
     const uint32_t sbo = (uint32_t)(KD / 8) * 128u;
     const uint32_t idesc = tc::idesc_bf16(128, sh.NC);
 
@@ -164,14 +173,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
         __syncthreads();
 
         for (int r = 0; r < sh.K; ++r) {
-            // ---- bring in B of RBM r ----
-            if (tid == 0) {
-                tc::mbar_expect_tx(&bars[0], sh.b_img_bytes);
-                tc::bulk_g2s(B, ta.bimg + (size_t)r * sh.NC * KD, sh.b_img_bytes, &bars[0]);
+            // ---- bring in B of RBM r (one tile: once per RBM) ----
+            if (sh.nmt == 1) {
+                if (tid == 0) {
+                    tc::mbar_expect_tx(&bars[0], sh.b_img_bytes);
+                    tc::bulk_g2s(B, ta.bimg + (size_t)r * sh.NC * KD, sh.b_img_bytes, &bars[0]);
+                }
+                const bool okb = tc::mbar_wait_bounded(&bars[0], ph_b);
+                ph_b ^= 1;
+                if (__syncthreads_or(!okb)) { aborted = true; if (tid == 0) atomicExch(md.status, -4); break; }
             }
-            const bool okb = tc::mbar_wait_bounded(&bars[0], ph_b);
-            ph_b ^= 1;
-            if (__syncthreads_or(!okb)) { aborted = true; if (tid == 0) atomicExch(md.status, -4); break; }
 
             for (int tile = 0; tile < sh.ntiles; ++tile) {
                 // ---- A: rows of this tile, K split between two threads per row ----
@@ -205,23 +216,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
                 }
                 tc::fence_proxy_async_smem();
                 __syncthreads();
-                // ---- MMAs: K/16 steps into TMEM columns [0, NC) ----
-                if (tid == 0) {
-                    tc::fence_after_sync();
-                    const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B);
-                    for (int kk = 0; kk < KD / 16; ++kk) {
-                        const uint64_t ad = tc::smem_desc(a0 + kk * 256u, 128u, sbo);
-                        const uint64_t bd = tc::smem_desc(b0 + kk * 256u, 128u, sbo);
-                        tc::mma_bf16(taddr, ad, bd, idesc, kk > 0 ? 1u : 0u);
-                    }
-                    tc::mma_commit(&bars[1]);
-                }
-                const bool okm = tc::mbar_wait_bounded(&bars[1], ph_m);
-                ph_m ^= 1;
-                if (__syncthreads_or(!okm)) { aborted = true; if (tid == 0) atomicExch(md.status, -4); break; }
-                tc::fence_after_sync();
-
-                // ---- epilogue: 2cosh products of this thread's half of the hidden units ----
                 const int row = quad * 32 + lane;
                 const int q = tile * 128 + row;
                 const int sl = q / G, g = q - sl * G;
@@ -229,31 +223,68 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
                 sc<float> pp{1.f, 0.f, 0}, pm{1.f, 0.f, 0};
                 const cx<float> *br = reinterpret_cast<const cx<float> *>(md.bvec) + (size_t)r * M;
                 const uint32_t lane_addr = taddr + ((uint32_t)(quad * 32) << 16);
-                const int cb = half ? c0 : 0, ce = half ? nchunk : c0;
-                for (int c = cb; c < ce; ++c) {
-                    float re[8], im[8];
-                    tc::tmem_ld8(lane_addr + (uint32_t)(c * 8), re);
-                    tc::tmem_ld8(lane_addr + (uint32_t)(M8 + c * 8), im);
-                    tc::tmem_wait_ld();
+                for (int mt = 0; mt < sh.nmt; ++mt) {
+                    if (sh.nmt > 1) {
+                        // ---- B of (RBM r, hidden-unit tile mt); the previous tile's MMAs are complete ----
+                        if (tid == 0) {
+                            tc::mbar_expect_tx(&bars[0], sh.b_img_bytes);
+                            tc::bulk_g2s(B, ta.bimg + ((size_t)r * sh.nmt + mt) * sh.NC * KD, sh.b_img_bytes,
+                                         &bars[0]);
+                        }
+                        const bool okb = tc::mbar_wait_bounded(&bars[0], ph_b);
+                        ph_b ^= 1;
+                        if (__syncthreads_or(!okb)) { aborted = true; if (tid == 0) atomicExch(md.status, -4); break; }
+                    }
+                    // ---- MMAs: K/16 steps into TMEM columns [0, NC) ----
+                    if (tid == 0) {
+                        tc::fence_after_sync();
+                        const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B);
+                        for (int kk = 0; kk < KD / 16; ++kk) {
+                            const uint64_t ad = tc::smem_desc(a0 + kk * 256u, 128u, sbo);
+                            const uint64_t bd = tc::smem_desc(b0 + kk * 256u, 128u, sbo);
+                            tc::mma_bf16(taddr, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        }
+                        tc::mma_commit(&bars[1]);
+                    }
+                    const bool okm = tc::mbar_wait_bounded(&bars[1], ph_m);
+                    ph_m ^= 1;
+                    if (__syncthreads_or(!okm)) { aborted = true; if (tid == 0) atomicExch(md.status, -4); break; }
+                    tc::fence_after_sync();
+
+                    // ---- epilogue: 2cosh products of this thread's half of the tile's hidden units ----
+                    const int cb = half ? c0 : 0, ce = half ? nchunk : c0;
+                    for (int c = cb; c < ce; ++c) {
+                        float re[8], im[8];
+                        tc::tmem_ld8(lane_addr + (uint32_t)(c * 8), re);
+                        tc::tmem_ld8(lane_addr + (uint32_t)(MT + c * 8), im);
+                        tc::tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int m = c * 8 + e;
-                        if (m < M) {
-                            cx<float> b{0.f, 0.f};
-                            if (md.use_bias) b = br[m];
-                            cx<float> mant;
-                            int k;
-                            cosh2_mant(cx<float>{b.x + re[e], b.y + im[e]}, mant, k);
-                            const cx<float> x = cmul(mk(pp.x, pp.y), mant);
-                            pp = sc_norm(sc<float>{x.x, x.y, pp.e + k});
-                            if (sh.nsign == 2) {
-                                cosh2_mant(cx<float>{b.x - re[e], b.y - im[e]}, mant, k);
-                                const cx<float> y = cmul(mk(pm.x, pm.y), mant);
-                                pm = sc_norm(sc<float>{y.x, y.y, pm.e + k});
+                        for (int e = 0; e < 8; ++e) {
+                            const int m = mt * MT + c * 8 + e;
+                            if (m < M) {
+                                cx<float> b{0.f, 0.f};
+                                if (md.use_bias) b = br[m];
+                                cx<float> mant;
+                                int k;
+                                cosh2_mant(cx<float>{b.x + re[e], b.y + im[e]}, mant, k);
+                                const cx<float> x = cmul(mk(pp.x, pp.y), mant);
+                                pp = sc_norm(sc<float>{x.x, x.y, pp.e + k});
+                                if (sh.nsign == 2) {
+                                    cosh2_mant(cx<float>{b.x - re[e], b.y - im[e]}, mant, k);
+                                    const cx<float> y = cmul(mk(pm.x, pm.y), mant);
+                                    pm = sc_norm(sc<float>{y.x, y.y, pm.e + k});
+                                }
                             }
                         }
                     }
+                    if (sh.nmt > 1) {
+                        // the next tile's MMAs overwrite TMEM and its copy overwrites B
+                        tc::fence_before_sync();
+                        __syncthreads();
+                        tc::fence_after_sync();
+                    }
                 }
+                if (aborted) break;
                 tc::fence_before_sync();
                 if (half == 1) { xbuf[2 * row] = pp; xbuf[2 * row + 1] = pm; }
                 __syncthreads();
@@ -354,7 +385,7 @@ static size_t tc_smem_bytes(const TcShape &s)
 
 bool tc_supported(int N, int M, int G, int K, int nsign, int NS)
 {
-    if (M > 128 || NS < 2 || NS > 3) return false;
+    if (M > kMaxM || NS < 2 || NS > 3) return false;
     const TcShape s = tc_shape(N, M, G, K, nsign, NS);
     return tc_smem_bytes(s) <= 220 * 1024 && s.KD <= 4096 && s.S <= 128;
 }
@@ -362,13 +393,13 @@ bool tc_supported(int N, int M, int G, int K, int nsign, int NS)
 size_t tc_bimg_bytes(int N, int M, int K, int NS)
 {
     const TcShape s = tc_shape(N, M, 1, K, 1, NS);
-    return (size_t)K * s.b_img_bytes;
+    return (size_t)K * s.nmt * s.b_img_bytes;
 }
 
 cudaError_t launch_bimg(const double *params, int N, int M, int K, int NS, uint16_t *img, cudaStream_t st)
 {
     const TcShape s = tc_shape(N, M, 1, K, 1, NS);
-    k_bimg<<<1024, 256, 0, st>>>(params, N, M, K, s.M8, NS, s.KD, img);
+    k_bimg<<<1024, 256, 0, st>>>(params, N, M, K, s.MT, s.nmt, NS, s.KD, img);
     return cudaGetLastError();
 }
 

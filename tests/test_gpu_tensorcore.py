@@ -1,5 +1,6 @@
 """log psi with the theta GEMM on the tcgen05 tensor cores (BF16-split
-weights) against the FP64 oracle and against the FP32 SIMT form.
+weights) against the FP64 oracle and against the FP32 SIMT form, for one
+hidden-unit tile (M <= 128) and several (M > 128, up to 10x10 K=4 M=400).
 
 Tolerance: |log psi| absolute <= 1e-5 (Im modulo 2 pi).  The split's error on
 theta is <= 2^-17 sum_j |W_mj| (two terms) or 2^-25 (three terms), and the
@@ -28,6 +29,10 @@ CASES = [
     (6, 1, 72, True, 1, True, 0, 0, 45, [(BF16X2, 0.01), (BF16X3, 0.01), (BF16X3, 0.05)]),
     (6, 1, 72, True, 0, False, 0, 0, 9, [(BF16X2, 0.01), (BF16X3, 0.05)]),
     (8, 1, 128, True, 0, True, 0, 0, 5, [(BF16X2, 0.01), (BF16X3, 0.05)]),
+    # M > 128: hidden units in tiles (2 x 104, 2 x 72, 4 x 128), one B image per tile
+    (4, 1, 200, False, 0, True, 0, 0, 300, [(BF16X2, 0.01), (BF16X3, 0.01)]),
+    (6, 1, 144, True, 1, True, 0, 0, 20, [(BF16X2, 0.01), (BF16X3, 0.01)]),
+    (4, 1, 512, True, 1, True, 0, 0, 10, [(BF16X3, 0.01)]),
 ]
 TOL_STRESS_LARGE = 1e-4   # 8x8, M = 128 at std 0.05 (accumulator rounding, see above)
 PARAMS = [(c[:9], ps) for c in CASES for ps in c[9]]
@@ -57,3 +62,19 @@ def test_tensor_core_matches_fp32_form_on_many_samples():
     c = nnqs.cfg_tensor(synth.pack(s))
     assert_logpsi_close(to_complex(g16.log_psi(c)), to_complex(g32.log_psi(c)), 1e-5)
     g16.status()
+
+
+def test_10x10_K4_M400_tensor_core():
+    """The 10x10 configuration (K = 4, M = 400 in four tiles of 104, |G| = 800):
+    three samples against the oracle, 512 against the FP32 SIMT form."""
+    from paper_2206_14307_gb300 import nnqs
+    om, g16, p = make_pair(10, K=4, M=400, proj=True, std=0.01, precision=BF16X2, logc_std=0.2)
+    g32 = nnqs.Model(10, 1.0, 0.5, K=4, M=400, proj_t=True, proj_p=True, precision=FP32)
+    g32.set_params(p)
+    s = synth.random_sz0(100, 600, seed=13)
+    s = s[~annihilated(10, s, True)][:512]
+    c = nnqs.cfg_tensor(synth.pack(s))
+    a = to_complex(g16.log_psi(c))
+    g16.status()
+    assert_logpsi_close(a, to_complex(g32.log_psi(c)), 1e-5)
+    assert_logpsi_close(a[:3], om.log_psi(s[:3]), 1e-5)
