@@ -60,13 +60,28 @@ N_SAMPLES = N_CHAINS * N_PER_CHAIN
 PARAM_STD, PARAM_SEED = 0.01, 2206
 WORKLOAD = "6x6 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=72), 288 ops + spin inversion; 1024 chains x 16 samples"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
-BF16_PEAK_TFLOPS = 1900.3   # measured dense bf16 burst figure of the GB300s
+
+
+def _measured_peaks():
+    """HBM GB/s and dense bf16 TFLOP/s (burst) measured on the GB300s,
+    from MEASURED_PEAKS.json beside this file; else the fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "of fallback"
+
+
+HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 FLOPS_PER_ELEMENT = 28   # one connected factor p e^D + (1-p) e^-D and its running product
 # DRAM bytes (read + write) per launch, from the ncu captures of the current
 # kernels on the 2048-sample (E_loc) and 512-sample (Lanczos) cases; the
 # traffic grows with the samples, so the full launches move 8x that.
 K_RATIO_TRAFFIC = 8 * 0.217856e6
 K_LANCZOS_TRAFFIC = 8 * 1.236224e6
+# k_sample: 9.214 GB written + 14.9 MB read per 128-chain launch, x8 for 1024 chains
+K_SAMPLE_TRAFFIC = 8 * (9.214206e9 + 14.924544e6)
 
 
 LZ_L, LZ_M, LZ_SAMPLES, LZ_SUBSET = 8, 128, 4096, 912   # subset: 6 x 152 SMs
@@ -213,7 +228,7 @@ def gpu_arm(args, rank, world):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        tot, tk, tl = 0.0, 0.0, 0.0
+        tot, tk, tl, ts = 0.0, 0.0, 0.0, 0.0
         for k in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -234,30 +249,31 @@ def gpu_arm(args, rank, world):
             ev[4].record(st)
             ev[4].synchronize()
             tot += ev[0].elapsed_time(ev[4])
+            ts += ev[0].elapsed_time(ev[1])
             tl += ev[1].elapsed_time(ev[2])
             tk += ev[2].elapsed_time(ev[3])
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        return tot / steps, tk / steps, tl / steps
+        return tot / steps, tk / steps, tl / steps, ts / steps
 
     m32 = make(nnqs.BF16X2)
     with ClockSampler(dev) as clk:
-        ms, ms_eloc, ms_logpsi = timed(m32, args.steps, args.warmup)
+        ms, ms_eloc, ms_logpsi, ms_sample = timed(m32, args.steps, args.warmup)
     m32.status()
-    e2e_ms, _, _ = timed(m32, args.steps, max(1, args.warmup // 2), e2e=True)
+    e2e_ms, _, _, _ = timed(m32, args.steps, max(1, args.warmup // 2), e2e=True)
     words = cfg.cpu().numpy().view(np.uint64)
     nb = n_antialigned(words)
     proposals = N_CHAINS * (N_BURN + N_PER_CHAIN * N_SKIP)
     evals = proposals + nb + N_SAMPLES
     G, nsign = m32.G, 2
     elements = nb * G * nsign * M
-    res = dict(ms=ms, ms_eloc=ms_eloc, ms_logpsi=ms_logpsi, e2e_ms=e2e_ms, evals=evals, nb=nb, elements=elements,
+    res = dict(ms=ms, ms_eloc=ms_eloc, ms_logpsi=ms_logpsi, ms_sample=ms_sample, e2e_ms=e2e_ms, evals=evals, nb=nb, elements=elements,
                clocks=clk.summary(), acc=float(acc.mean().item()), e_mean=float(eloc[:, 0].mean().item()) / N,
                G=G)
     if not args.no_fp64:
         m64 = make(nnqs.FP64)
-        ms64, ms64_eloc, ms64_logpsi = timed(m64, args.fp64_steps, 1)
+        ms64, ms64_eloc, ms64_logpsi, _ = timed(m64, args.fp64_steps, 1)
         res.update(ms64=ms64, ms64_eloc=ms64_eloc, ms64_logpsi=ms64_logpsi)
         m64.close()
     m32.close()
@@ -487,6 +503,12 @@ def main():
     # theta GEMM: algorithmic 4 K|G| M N flop per fresh amplitude (complex W times +-1 configurations)
     gemm_flop = 4.0 * res["G"] * M * N * N_SAMPLES
     gemm_ach = gemm_flop / (res["ms_logpsi"] / 1e3) / 1e12
+    # sampler: per proposal the cache of p (complex64 per (row, sign, m)) is read
+    # and its speculative update written, and the row terms (12 B each) likewise
+    rs_pairs = res["G"] * 2
+    samp_per = 16 * rs_pairs * M + 24 * rs_pairs
+    proposals = N_CHAINS * (N_BURN + N_PER_CHAIN * N_SKIP)
+    samp_bytes = float(proposals) * samp_per
     line = {
         "metric": "projected-RBM amplitude evals/s (E_loc samples/s beside); BF16-split/FP32 form vs plain FP64 GPU form",
         "value": value, "unit": "amplitude evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -504,10 +526,16 @@ def main():
                      "work": f"{res['elements']} connected elements x {FLOPS_PER_ELEMENT} flop"},
         "theta_gemm": {"kernel": "k_logpsi_tc (tcgen05 theta GEMM + fused log-cosh epilogue)", "bound": "tensor",
                        "achieved": gemm_ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "frac": gemm_ach / BF16_PEAK_TFLOPS, "peak_source": "MEASURED bf16 burst (of measured)",
+                       "frac": gemm_ach / BF16_PEAK_TFLOPS, "peak_source": f"bf16 dense burst ({PEAK_SOURCE})",
                        "fresh_amplitudes_per_s": N_SAMPLES / (res["ms_logpsi"] / 1e3),
                        "note": "algorithmic flop (4 K|G| M N per amplitude); the bf16 hi+lo split executes 2x; "
                                "the kernel is limited by its log-cosh epilogue, not the MMA"},
+        "sampler": {"kernel": "k_sample (Metropolis proposals with the speculative p-cache update)", "bound": "hbm",
+                    "achieved": samp_bytes / (res["ms_sample"] / 1e3) / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                    "frac": samp_bytes / (res["ms_sample"] / 1e3) / 1e9 / HBM_PEAK_GBS,
+                    "peak_source": f"HBM copy bandwidth ({PEAK_SOURCE})", "traffic": K_SAMPLE_TRAFFIC,
+                    "work": f"{proposals} proposals x {samp_per} B of cache read and written",
+                    "ms": res["ms_sample"]},
         "e2e": {"value": world * res["evals"] / (e2e_ms / 1e3), "unit": "amplitude evals/s",
                 "h2d_bytes_per_step": 2665 * 16, "d2h_bytes_per_step": 32},
         "gpu_launches": 5 * args.steps,
@@ -548,7 +576,7 @@ def main():
             "kernel": "k_logpsi_tc (4 hidden-unit tiles of 104)", "bound": "tensor",
             "fresh_amplitudes_per_s": 8192 / (t["bf16x2"] / 1e3), "ms": t["bf16x2"],
             "achieved": ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / BF16_PEAK_TFLOPS,
-            "peak_source": "MEASURED bf16 burst (of measured)",
+            "peak_source": f"bf16 dense burst ({PEAK_SOURCE})",
             "fp32_simt": {"fresh_amplitudes_per_s": 8192 / (t["fp32"] / 1e3), "ms": t["fp32"]},
             "speedup_vs_fp32_simt": t["fp32"] / t["bf16x2"]}
     if "mixed" in res:
