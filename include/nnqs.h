@@ -83,6 +83,16 @@ typedef struct nnqs_desc {
     int32_t spin_inversion;       /* 0 = off, +1 / -1 = character chi_P */
     int32_t use_bias;             /* 1: Eq. 2 with a, b; 0: bias-free Eq. 3 */
     int32_t precision;            /* NNQS_FP64 .. NNQS_BF16X3 */
+    int32_t check_inputs;         /* 1: checked mode -- every call that takes
+                                     configurations first verifies that each lies
+                                     in the Sz = 0 sector the method samples
+                                     (Sec. 3.2: N/2 bits set, none past site
+                                     N - 1) and returns NNQS_EINVAL, naming the
+                                     first offending index, otherwise.  The check
+                                     runs on the device and synchronises the
+                                     stream once per call.  0: no check (the
+                                     default; results for such inputs are
+                                     undefined). */
 } nnqs_desc;
 
 typedef struct nnqs_model nnqs_model;
@@ -134,13 +144,16 @@ int nnqs_sample(nnqs_model *model, uint64_t seed, int32_t n_chains, int32_t n_pe
                 int32_t n_skip, int32_t n_burn, uint64_t *cfg_out, float *acc_out, void *stream);
 
 /* log psi(s) for n configurations (Eqs. 2-6): logpsi_out [n][2] doubles
- * (re, im), Im in (-pi, pi].  cfg: [n][ceil(N/64)].  With NNQS_BF16X2/X3 and
- * M <= 128 the theta products of all n*K*|G| transformed configurations run
- * on the tcgen05 tensor cores (bf16 split weights, fp32 accumulation in
- * TMEM) with the log-cosh and projection sums fused into the epilogue; other
- * sizes use the FP32 form.  Accuracy of theta: 2^-17 (two terms) or 2^-25
- * (three terms) relative to sum_j |W_mj|.  A configuration whose amplitude
- * vanishes by symmetry returns re = -inf. */
+ * (re, im), Im in (-pi, pi].  cfg: [n][ceil(N/64)].  With NNQS_BF16X2/X3 the
+ * theta products of all n*K*|G| transformed configurations run on the
+ * tcgen05 tensor cores (bf16 split weights, fp32 accumulation in TMEM) for
+ * every M up to the model limit of 512: the hidden units are taken in tiles of
+ * at most 128, whose products multiply into each row's running product; the
+ * log-cosh and projection sums are fused into the epilogue.  A shape whose
+ * tiles do not fit the shared memory of one SM uses the FP32 form.  Accuracy
+ * of theta: 2^-17 (two terms) or 2^-25 (three terms) relative to
+ * sum_j |W_mj|.  A configuration whose amplitude vanishes by symmetry returns
+ * re = -inf. */
 int nnqs_log_psi(nnqs_model *model, const uint64_t *cfg, int64_t n, double *logpsi_out, void *stream);
 
 /* Local energy (Sec. 3.2, Eq. 10): E_loc(s) = sum_s' H_{s s'} psi(s')/psi(s)

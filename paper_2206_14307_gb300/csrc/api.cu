@@ -128,6 +128,7 @@ struct nnqs_model {
     uint16_t *bimg = nullptr;    // shared-memory images of the split weights
     uint8_t *pinv = nullptr;     // inverse permutations [G][N]
     int *status = nullptr;
+    unsigned long long *chk = nullptr;  // checked mode: first configuration outside Sz = 0
     void *ws = nullptr;
     size_t ws_bytes = 0;
 };
@@ -187,6 +188,28 @@ template <typename F> int with_device(const nnqs_model *m, F &&f)
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Checked mode (desc.check_inputs): rejects a batch of configurations with
+// NNQS_EINVAL if any lies outside the Sz = 0 sector or sets bits past site
+// N - 1.  Runs one small kernel and synchronises the stream; a no-op when the
+// mode is off.  Called with the model's device current.
+int check_cfg(const nnqs_model *m, const uint64_t *cfg, int64_t n, cudaStream_t st)
+{
+    if (!m->d.check_inputs || n <= 0) return NNQS_OK;
+    cudaError_t e = launch_check_sz0(cfg, n, m->nwords, m->N, m->chk, st);
+    unsigned long long bad = ~0ull;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, m->chk, sizeof bad, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "input check");
+    if (bad == ~0ull) return NNQS_OK;
+    uint64_t w[kMaxWords] = {};
+    e = cudaMemcpy(w, cfg + (size_t)bad * m->nwords, (size_t)m->nwords * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "input check");
+    int up = 0;
+    for (int k = 0; k < m->nwords; ++k) up += __builtin_popcountll(w[k]);
+    return fail(NNQS_EINVAL, "configuration %llu is not a valid Sz = 0 state of %d sites (%d bits set)", bad, m->N,
+                up);
+}
 
 }  // namespace
 
@@ -259,6 +282,7 @@ static int create_model(const nnqs_desc *desc, int mp_min, nnqs_model **out)
     ALLOC(m->ES, K * 2 * N * (m->fp64 ? sizeof(sc<double>) : sizeof(sc<float>)));
     ALLOC(m->bperm, (size_t)m->G * bi.size() * sizeof(uint16_t));
     ALLOC(m->status, sizeof(int));
+    ALLOC(m->chk, sizeof(unsigned long long));
     if (d.precision == NNQS_BF16X2 || d.precision == NNQS_BF16X3) {
         const int ns = d.precision == NNQS_BF16X2 ? 2 : 3;
         if (tc_supported((int)N, d.M, m->G, d.K, m->nsign, ns)) {
@@ -317,7 +341,7 @@ int nnqs_destroy(nnqs_model *m)
     if (!m) return NNQS_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {m->perm, m->bi, m->bj, m->bt, m->chi, m->params, m->Wt, m->b, m->a, m->logc, m->X, m->XA,
-                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->ws, m->bimg, m->pinv};
+                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->chk, m->ws, m->bimg, m->pinv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -384,6 +408,7 @@ int nnqs_log_psi(nnqs_model *m, const uint64_t *cfg, int64_t n, double *out, voi
     if (!cfg || !out) return fail(NNQS_EINVAL, "cfg and logpsi_out must be non-NULL");
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
+        if (int rc = check_cfg(m, cfg, n, st)) return rc;
         cudaError_t e;
         if (m->fp64) e = launch_log_psi(view<double>(m), cfg, n, out, m->nsm, st);
         else if (m->ns) e = launch_log_psi_tc(view<float>(m), m->bimg, m->pinv, m->ns, cfg, n, out, m->nsm, st);
@@ -400,6 +425,7 @@ int nnqs_local_energy(nnqs_model *m, const uint64_t *cfg, int64_t n, double *elo
     if (!cfg || !eloc) return fail(NNQS_EINVAL, "cfg and eloc_out must be non-NULL");
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
+        if (int rc = check_cfg(m, cfg, n, st)) return rc;
         cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 0, eloc, nullptr, m->nsm, st)
                                 : launch_ratio(view<float>(m), cfg, n, 0, eloc, nullptr, m->nsm, st);
         if (e != cudaSuccess) return cuda_fail(e, "local_energy");
@@ -424,6 +450,7 @@ int nnqs_lanczos_moments(nnqs_model *m, const uint64_t *cfg, int64_t n, double *
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
         const int nb = 64;
+        if (int rc = check_cfg(m, cfg, n, st)) return rc;
         size_t need = align256(nb * kMomentSums * sizeof(double));
         const size_t off_h1 = need;
         if (!h1) need += align256((size_t)n * 2 * sizeof(double));
@@ -477,6 +504,7 @@ int nnqs_grad_logpsi(nnqs_model *m, const uint64_t *cfg, int64_t n, double *O, v
     if ((size_t)m->G * m->N > 200 * 1024) return fail(NNQS_EUNSUPPORTED, "|G| * N too large for the gradient kernel");
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
+        if (int rc = check_cfg(m, cfg, n, st)) return rc;
         cudaError_t e;
         if (m->fp64) {
             const DevModel<double> v = view<double>(m);
@@ -596,6 +624,7 @@ int nnqs_lanczos_moments_noalloc(nnqs_model *m, const uint64_t *cfg, int64_t n, 
         double *h1 = base, *h2 = base + 2 * (size_t)NNQS_NOALLOC_MAX_SAMPLES;
         double *partial = base + 4 * (size_t)NNQS_NOALLOC_MAX_SAMPLES;
         cudaStream_t st = (cudaStream_t)stream;
+        if (int rc = check_cfg(m, cfg, n, st)) return rc;
         cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, h1, h2, m->nsm, st)
                                 : launch_ratio(view<float>(m), cfg, n, 1, h1, h2, m->nsm, st);
         if (e != cudaSuccess) return cuda_fail(e, "lanczos (fixed scratch)");
@@ -617,6 +646,7 @@ int nnqs_lanczos2(nnqs_model *m, const uint64_t *cfg, int64_t n, double *h3_out,
     if (tmax > 0x7fffffffLL) return fail(NNQS_EINVAL, "too many neighbour configurations (n x 4N >= 2^31)");
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
+        if (int rc = check_cfg(m, cfg, n, st)) return rc;
         // workspace: every piece 256-byte aligned, sized for the upper bound of neighbours
         size_t at = 0;
         auto take = [&](size_t bytes) { const size_t o = at; at += align256(bytes); return o; };
@@ -686,6 +716,7 @@ int nnqs_structure_factor(nnqs_model *m, const uint64_t *cfg, int64_t n, const d
     if (n < 1) return fail(NNQS_EINVAL, "n must be >= 1");
     if (!cfg || !sq_out) return fail(NNQS_EINVAL, "cfg and sq_out must be non-NULL");
     return with_device(m, [&]() -> int {
+        if (int rc = check_cfg(m, cfg, n, (cudaStream_t)stream)) return rc;
         const int grid = sq_grid(n, m->nsm);
         int rc = ensure_ws(m, (size_t)grid * (m->N + 1) * sizeof(double));
         if (rc) return rc;
@@ -809,6 +840,18 @@ void batch_offsets(const nnqs_batch *b, const int64_t *n, std::vector<int64_t> &
     }
 }
 
+// Checked mode of the instances that asked for it (desc.check_inputs).
+int batch_check_cfg(const nnqs_batch *b, const uint64_t *cfg, const int64_t *n, cudaStream_t st)
+{
+    std::vector<int64_t> cfg_off, out_off;
+    batch_offsets(b, n, cfg_off, out_off);
+    for (size_t i = 0; i < b->models.size(); ++i) {
+        if (int rc = check_cfg(b->models[i], cfg + cfg_off[i], n[i], st))
+            return fail(rc, "instance %zu: %s", i, std::string(g_err).c_str());
+    }
+    return NNQS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -925,6 +968,7 @@ int nnqs_batch_lanczos(nnqs_batch *b, const uint64_t *cfg, const int64_t *n_per_
     const size_t nm = b->models.size();
     return with_device(b->models[0], [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
+        if (int rc = batch_check_cfg(b, cfg, n_per_model, st)) return rc;
         if (!h1_out || !h2_out) {
             if (int rc = grow(b->d_h, b->h_cap, (size_t)4 * (total > 0 ? total : 1))) return rc;
         }
@@ -985,6 +1029,7 @@ int nnqs_batch_autotune(nnqs_batch *b, const uint64_t *cfg, const int64_t *n_per
     const size_t nm = b->models.size();
     return with_device(b->models[0], [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
+        if (int rc = batch_check_cfg(b, cfg, n_per_model, st)) return rc;
         std::vector<int64_t> cfg_off, out_off;
         batch_offsets(b, n_per_model, cfg_off, out_off);
         const int R = b->grid;  // one item per resident CTA: a full-load wave

@@ -160,6 +160,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
     const uint32_t taddr = *tmem_base;
     uint32_t ph_b = 0, ph_m = 0;
     bool aborted = false;  // uniform over the CTA (set from __syncthreads_or)
+    // this thread's view of work still in flight after a timed-out wait (the
+    // phase bits are flipped only on success, so they still name that phase)
+    bool mma_pending = false, copy_pending = false;
 
     const int64_t nsuper = (n + sh.S - 1) / sh.S;
     for (int64_t st = blockIdx.x; st < nsuper; st += gridDim.x) {
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
                     tc::bulk_g2s(B, ta.bimg + (size_t)r * sh.NC * KD, sh.b_img_bytes, &bars[0]);
                 }
                 const bool okb = tc::mbar_wait_bounded(&bars[0], ph_b);
-                ph_b ^= 1;
+                if (okb) ph_b ^= 1; else copy_pending = true;
                 if (__syncthreads_or(!okb)) { aborted = true; if (tid == 0) atomicExch(md.status, -4); break; }
             }
 
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
                                          &bars[0]);
                         }
                         const bool okb = tc::mbar_wait_bounded(&bars[0], ph_b);
-                        ph_b ^= 1;
+                        if (okb) ph_b ^= 1; else copy_pending = true;
                         if (__syncthreads_or(!okb)) { aborted = true; if (tid == 0) atomicExch(md.status, -4); break; }
                     }
                     // ---- MMAs: K/16 steps into TMEM columns [0, NC) ----
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
                         tc::mma_commit(&bars[1]);
                     }
                     const bool okm = tc::mbar_wait_bounded(&bars[1], ph_m);
-                    ph_m ^= 1;
+                    if (okm) ph_m ^= 1; else mma_pending = true;
                     if (__syncthreads_or(!okm)) { aborted = true; if (tid == 0) atomicExch(md.status, -4); break; }
                     tc::fence_after_sync();
 
@@ -364,9 +367,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logpsi_tc(DevModel<T> md, TcA
         }
         __syncthreads();
     }
-    if (aborted) {
-        // let any MMA still in flight finish before the accumulator is freed
-        (void)tc::mbar_wait_bounded(&bars[1], ph_m, 1u << 20);
+    if (aborted && tid == 0) {
+        // the issuing thread lets its MMAs and its bulk copy still in flight
+        // finish (bounded) before the accumulator is freed and the CTA exits
+        if (mma_pending) (void)tc::mbar_wait_bounded(&bars[1], ph_m, 1u << 22);
+        if (copy_pending) (void)tc::mbar_wait_bounded(&bars[0], ph_b, 1u << 22);
     }
     tc::fence_before_sync();
     __syncthreads();

@@ -54,6 +54,36 @@ __global__ void __launch_bounds__(kRedThreads) k_moments_partial(const double *_
         for (int q = 0; q < kMomentSums; ++q) partial[blockIdx.x * kMomentSums + q] = v[q];
 }
 
+// Checked mode of the boundary: the first configuration (lowest index) that is
+// not in the Sz = 0 sector (popcount != N/2) or has bits set past site N - 1;
+// first_bad must hold UINT64_MAX on entry and keeps it if all are valid.
+__global__ void k_check_sz0(const uint64_t *__restrict__ cfg, int64_t n, int nwords, int N,
+                            unsigned long long *__restrict__ first_bad)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        int pc = 0;
+        bool stray = false;
+        for (int w = 0; w < nwords; ++w) {
+            const uint64_t x = cfg[k * nwords + w];
+            pc += __popcll(x);
+            const int lo = 64 * w, valid = N - lo < 64 ? N - lo : 64;   // sites of this word
+            if (valid < 64 && (x >> valid) != 0ull) stray = true;
+        }
+        if (stray || 2 * pc != N) atomicMin(first_bad, (unsigned long long)k);
+    }
+}
+
+cudaError_t launch_check_sz0(const uint64_t *cfg, int64_t n, int nwords, int N, unsigned long long *first_bad,
+                             cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(first_bad, 0xff, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || n <= 0) return e;
+    const int64_t want = (n + kRedThreads - 1) / kRedThreads;
+    const int grid = (int)(want < 1024 ? want : 1024);
+    k_check_sz0<<<grid, kRedThreads, 0, st>>>(cfg, n, nwords, N, first_bad);
+    return cudaGetLastError();
+}
+
 // stage 2: fixed-order sum of the partials, moments and the p = 1 Lanczos step
 __global__ void __launch_bounds__(32) k_moments_final(const double *__restrict__ partial, int nb,
                                                       double *__restrict__ moments, double *__restrict__ lanczos)

@@ -83,6 +83,11 @@ template <typename T>
 cudaError_t launch_grad(const DevModel<T> &md, const uint64_t *cfg, int64_t n, double *O, void *scratch, int grid,
                         cudaStream_t st);
 
+// checked mode: first_bad <- lowest index of a configuration outside Sz = 0
+// (UINT64_MAX if none)
+cudaError_t launch_check_sz0(const uint64_t *cfg, int64_t n, int nwords, int N, unsigned long long *first_bad,
+                             cudaStream_t st);
+
 // FP64 reductions
 cudaError_t launch_moments(const double *h1, const double *h2, int64_t n, double *partial, int nblocks,
                            double *moments, double *lanczos, cudaStream_t st);

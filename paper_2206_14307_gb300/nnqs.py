@@ -42,7 +42,7 @@ class nnqs_desc(ctypes.Structure):
                 ("project_translations", ctypes.c_int32), ("project_point_group", ctypes.c_int32),
                 ("momentum", ctypes.c_int32), ("irrep", ctypes.c_int32),
                 ("spin_inversion", ctypes.c_int32), ("use_bias", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("check_inputs", ctypes.c_int32)]
 
 
 class NNQSError(RuntimeError):
@@ -225,12 +225,12 @@ class Model:
     complex results float64 [n][2]."""
 
     def __init__(self, L, J1=1.0, J2=0.5, K=1, M=None, proj_t=False, proj_p=False, momentum=K00, irrep=A1,
-                 spin_inv=0, use_bias=True, precision=FP32):
+                 spin_inv=0, use_bias=True, precision=FP32, check_inputs=False):
         self.L, self.N = L, L * L
         self.M = M if M is not None else self.N
         self.K = K
         self.desc = nnqs_desc(L, J1, J2, K, self.M, int(proj_t), int(proj_p), momentum, irrep,
-                              spin_inv, int(use_bias), precision)
+                              spin_inv, int(use_bias), precision, int(check_inputs))
         self.h = nnqs_create(self.desc)
         self.P = nnqs_num_params(self.h)
         self.G = nnqs_group_size(self.h)
@@ -382,7 +382,8 @@ class Batch:
             descs.append(nnqs_desc(L, sp.get("J1", 1.0), sp.get("J2", 0.5), sp.get("K", 1), M,
                                    int(sp.get("proj_t", False)), int(sp.get("proj_p", False)),
                                    sp.get("momentum", K00), sp.get("irrep", A1), sp.get("spin_inv", 0),
-                                   int(sp.get("use_bias", True)), sp.get("precision", FP32)))
+                                   int(sp.get("use_bias", True)), sp.get("precision", FP32),
+                                   int(sp.get("check_inputs", False))))
         self.h = nnqs_batch_create(descs)
         self.models = [_Borrowed(nnqs_batch_model(self.h, i), d) for i, d in enumerate(descs)]
 
