@@ -60,7 +60,6 @@ N_SAMPLES = N_CHAINS * N_PER_CHAIN
 PARAM_STD, PARAM_SEED = 0.01, 2206
 METRIC = "projected-RBM amplitude evals/s; Lanczos E_loc samples/s vs FP64 GPU form"
 WORKLOAD = "6x6 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=72), 288 ops + spin inversion; 1024 chains x 16 samples"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
 
 
 def _measured_peaks():
@@ -75,6 +74,27 @@ def _measured_peaks():
 
 
 HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
+
+
+def _alu_peaks():
+    """FP32 FMA / MUFU / FP64 peaks measured on this machine's GB300 by the
+    microbenchmark summarised in profiles/alu_peaks_gb300.md (its JSON line);
+    else the peak derived from the unit counts and the maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "alu_peaks_gb300.md")) as f:
+            for line in f:
+                if line.startswith("{") and "fp32_fma_tflops" in line:
+                    d = json.loads(line)
+                    return d, "measured (profiles/alu_peaks_gb300.md)"
+    except (OSError, ValueError):
+        pass
+    return {"fp32_fma_tflops": 152 * 128 * 2 * 2.070e9 / 1e12, "mufu_ex2_gops": 152 * 16 * 2.070,
+            "fp64_fma_tflops": 1.25}, "derived from unit counts x 2070 MHz"
+
+
+ALU_PEAKS, ALU_SOURCE = _alu_peaks()
+FP32_PEAK_TFLOPS = float(ALU_PEAKS["fp32_fma_tflops"])
+MUFU_EX2_GOPS = float(ALU_PEAKS["mufu_ex2_gops"])
 # Method work per connected element: f = 1 + p T (a complex multiply-add) and
 # the running product prod *= f (a complex multiply), i.e. 8 FMA-pipe issue
 # slots = 16 peak-equivalent flop.
@@ -111,8 +131,9 @@ def n_antialigned(words):
 
 def rank_seed(rank, k):
     """Sampler seed of step k on a rank: ranks draw disjoint Philox streams, so
-    N ranks run N times the chains (weak scaling, no collective on the data
-    path)."""
+    N ranks run N times the chains (weak scaling); the one exchange on the
+    data path is the all-reduce of the FP64 sums (E_loc sums, Lanczos
+    moments), which makes the job's estimate one over all ranks' samples."""
     return 14307 + 1000003 * rank + k
 
 
@@ -223,6 +244,7 @@ def gpu_arm(args, rank, world):
         model.sample(seed, N_CHAINS, N_PER_CHAIN, N_SKIP, N_BURN, cfg_out=cfg, acc_out=acc)
         model.log_psi(cfg, out=logpsi)
         model.local_energy(cfg, out=eloc, sums=sums)
+        nnqs.allreduce_sums(sums)
         if e2e:
             sums_host.copy_(sums, non_blocking=True)
 
@@ -247,6 +269,7 @@ def gpu_arm(args, rank, world):
             model.log_psi(cfg, out=logpsi)
             ev[2].record(st)
             model.local_energy(cfg, out=eloc, sums=sums)
+            nnqs.allreduce_sums(sums)   # one E_loc estimate over every rank's chains (no-op on one process)
             ev[3].record(st)
             if e2e:
                 sums_host.copy_(sums, non_blocking=True)
@@ -326,7 +349,15 @@ def lanczos_leg(args, rank, flush):
     h2 = torch.empty_like(h1)
     mo = torch.empty(8, dtype=torch.float64, device="cuda")
     lz = torch.empty(3, dtype=torch.float64, device="cuda")
-    full = lambda: m32.lanczos(cfg, h1, h2, mo, lz)
+    sums = torch.empty(7, dtype=torch.float64, device="cuda")
+
+    def full():
+        # partial sums of this rank's samples, their all-reduce over the ranks
+        # (no-op on one process), the closed form: one E_p1 over all samples
+        m32.lanczos_partial(cfg, h1, h2, sums)
+        nnqs.allreduce_sums(sums)
+        nnqs.lanczos_finish(sums, mo, lz)
+
     full()
     ms_full = _event_ms(full, flush, max(1, args.lanczos_steps))
     e_p1 = float(lz[0].item()) / Nl
@@ -545,7 +576,7 @@ def main():
         "roofline": {"kernel": "k_eloc (E_loc connected-amplitude engine)", "bound": "alu",
                      "achieved": eloc_ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": eloc_ach / FP32_PEAK_TFLOPS, "traffic": K_RATIO_TRAFFIC,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",
+                     "peak_source": f"FP32 FMA, {ALU_SOURCE}",
                      "work": f"{res['elements']} connected elements x {FLOPS_PER_ELEMENT} flop"},
         "theta_gemm": {"kernel": "k_logpsi_tc (tcgen05 theta GEMM + fused log-cosh epilogue)", "bound": "tensor",
                        "achieved": gemm_ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -178,6 +178,24 @@ int nnqs_local_energy(nnqs_model *model, const uint64_t *cfg, int64_t n, double 
 int nnqs_lanczos_moments(nnqs_model *model, const uint64_t *cfg, int64_t n, double *h1_out,
                          double *h2_out, double *moments_out, double *lanczos_out, void *stream);
 
+/* The Lanczos step of nnqs_lanczos_moments split for samples spread over
+ * several processes (one GPU each; the samples of |psi|^2 are independent,
+ * Sec. 3.2, so each process draws and evaluates its own chains).
+ *
+ * nnqs_lanczos_partial: h1 and h2 of this process's n configurations (h1_out,
+ * h2_out: [n][2], either may be NULL) and their raw FP64 sums
+ *   sums_out[0..6] = {n, sum Re h1, sum |h1|^2, sum Re(conj(h1) h2),
+ *                     sum Im h1, sum Im(conj(h1) h2), sum |h2|^2}
+ * (device [7]; n = 0 gives zeros).  Add sums_out element-wise over all
+ * processes (an all-reduce of 7 doubles, e.g. NCCL on the same stream), then
+ * nnqs_lanczos_finish: from the summed sums (device [7]) the moments_out [8]
+ * and lanczos_out [3] of nnqs_lanczos_moments over the union of all samples
+ * (either output may be NULL).  On one process the two calls give the result
+ * of nnqs_lanczos_moments to FP64 rounding. */
+int nnqs_lanczos_partial(nnqs_model *model, const uint64_t *cfg, int64_t n, double *h1_out, double *h2_out,
+                         double *sums_out, void *stream);
+int nnqs_lanczos_finish(const double *sums, double *moments_out, double *lanczos_out, void *stream);
+
 /* The p = 2 Lanczos step (Sec. 3.3: |Psi_2> = (1 + beta_1 H + beta_2 H^2)|psi0>).
  * Per configuration
  *   h3 = (H^3 psi)(s)/psi(s) = diag(s) h2(s) + sum_b (J_b/2) [psi(s^b)/psi(s)] h2(s^b)

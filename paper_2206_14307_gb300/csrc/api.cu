@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <cstring>
 #include <string>
@@ -115,6 +116,7 @@ struct nnqs_model {
     int Mp;  // row stride of the connected-configuration tables
     int64_t P;
     bool fp64;
+    bool can_vanish;  // some group element carries character -1: amplitudes can vanish by symmetry
     uint8_t *perm = nullptr;
     int16_t *bi = nullptr, *bj = nullptr;
     uint8_t *bt = nullptr;
@@ -126,7 +128,7 @@ struct nnqs_model {
     // tensor-core path (NNQS_BF16X2 / NNQS_BF16X3)
     int ns = 0;                  // bf16 terms of the split (0: tensor-core path off)
     uint16_t *bimg = nullptr;    // shared-memory images of the split weights
-    uint8_t *pinv = nullptr;     // inverse permutations [G][N]
+    uint16_t *pinv = nullptr;    // inverse permutations [G][round16(N)]
     int *status = nullptr;
     unsigned long long *chk = nullptr;  // checked mode: first configuration outside Sz = 0
     void *ws = nullptr;
@@ -153,9 +155,23 @@ template <typename T> DevModel<T> view(const nnqs_model *m)
     return v;
 }
 
+// Test hook: NNQS_TEST_WORKSPACE_CAP=<bytes> makes every workspace growth
+// beyond that size fail as a refused allocation (NNQS_ENOMEM).  Unset in
+// normal use.
+size_t workspace_cap()
+{
+    const char *v = getenv("NNQS_TEST_WORKSPACE_CAP");
+    if (!v || !*v) return (size_t)-1;
+    char *end = nullptr;
+    const unsigned long long c = strtoull(v, &end, 10);
+    return (end && *end == 0) ? (size_t)c : (size_t)-1;
+}
+
 int ensure_ws(nnqs_model *m, size_t bytes)
 {
     if (bytes <= m->ws_bytes) return NNQS_OK;
+    if (bytes > workspace_cap())
+        return fail(NNQS_ENOMEM, "workspace of %zu bytes refused (test cap %zu)", bytes, workspace_cap());
     if (m->ws) {
         cudaDeviceSynchronize();
         cudaFree(m->ws);
@@ -189,6 +205,12 @@ template <typename F> int with_device(const nnqs_model *m, F &&f)
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Post-pass for configurations annihilated by the projection (models with a
+// character -1 only): log psi = -inf (mode 0); E_loc / h1 / h2 = NaN and
+// NNQS_ERANGE in the status word (mode 1).
+cudaError_t mark_vanishing(const nnqs_model *m, const uint64_t *cfg, int64_t n, int mode, double *o1, double *o2,
+                           cudaStream_t st);
+
 // Checked mode (desc.check_inputs): rejects a batch of configurations with
 // NNQS_EINVAL if any lies outside the Sz = 0 sector or sets bits past site
 // N - 1.  Runs one small kernel and synchronises the stream; a no-op when the
@@ -209,6 +231,14 @@ int check_cfg(const nnqs_model *m, const uint64_t *cfg, int64_t n, cudaStream_t 
     for (int k = 0; k < m->nwords; ++k) up += __builtin_popcountll(w[k]);
     return fail(NNQS_EINVAL, "configuration %llu is not a valid Sz = 0 state of %d sites (%d bits set)", bad, m->N,
                 up);
+}
+
+cudaError_t mark_vanishing(const nnqs_model *m, const uint64_t *cfg, int64_t n, int mode, double *o1, double *o2,
+                           cudaStream_t st)
+{
+    if (!m->can_vanish || n <= 0) return cudaSuccess;
+    return m->fp64 ? launch_mark_vanishing(view<double>(m), cfg, n, mode, o1, o2, st)
+                   : launch_mark_vanishing(view<float>(m), cfg, n, mode, o1, o2, st);
 }
 
 }  // namespace
@@ -253,6 +283,11 @@ static int create_model(const nnqs_desc *desc, int mp_min, nnqs_model **out)
     make_bonds(d.L, bi, bj, bt);
     m->nbonds = (int)bi.size();
     m->G = make_group(d, perm, chi);
+    {
+        const int inv_char = d.spin_inversion ? d.spin_inversion : (d.use_bias ? 0 : 1);
+        m->can_vanish = inv_char < 0;
+        for (double c : chi) m->can_vanish = m->can_vanish || c < 0;
+    }
 
     auto cleanup = [&](int rc) { nnqs_destroy(m); return rc; };
     const size_t ts = m->fp64 ? sizeof(double) : sizeof(float);
@@ -287,17 +322,16 @@ static int create_model(const nnqs_desc *desc, int mp_min, nnqs_model **out)
         const int ns = d.precision == NNQS_BF16X2 ? 2 : 3;
         if (tc_supported((int)N, d.M, m->G, d.K, m->nsign, ns)) {
             m->ns = ns;
-            ALLOC(m->bimg, tc_bimg_bytes((int)N, d.M, d.K, ns));
-            ALLOC(m->pinv, (size_t)m->G * N);
+            ALLOC(m->bimg, tc_bimg_bytes((int)N, d.M, m->G, d.K, m->nsign, ns));
+            ALLOC(m->pinv, tc_pinv_bytes((int)N, m->G));
         }
     }
 #undef ALLOC
     cudaMemcpy(m->perm, perm.data(), perm.size(), cudaMemcpyHostToDevice);
     if (m->pinv) {
-        std::vector<uint8_t> inv(perm.size());
-        for (int g = 0; g < m->G; ++g)
-            for (int i = 0; i < m->N; ++i) inv[(size_t)g * m->N + perm[(size_t)g * m->N + i]] = (uint8_t)i;
-        cudaMemcpy(m->pinv, inv.data(), inv.size(), cudaMemcpyHostToDevice);
+        std::vector<uint16_t> inv(tc_pinv_bytes(m->N, m->G) / sizeof(uint16_t));
+        tc_pinv_table(perm.data(), m->N, m->G, inv.data());
+        cudaMemcpy(m->pinv, inv.data(), inv.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     }
     {
         // image of every bond under every group element, with the orientation flag
@@ -380,7 +414,7 @@ int nnqs_set_params_device(nnqs_model *m, const double *params, int64_t P, void 
                                           (cx<float> *)m->CS, (sc<float> *)m->ES, st);
         if (e != cudaSuccess) return cuda_fail(e, "build connection tables");
         if (m->ns) {
-            e = launch_bimg(m->params, m->N, m->d.M, m->d.K, m->ns, m->bimg, st);
+            e = launch_bimg(m->params, m->N, m->d.M, m->G, m->d.K, m->nsign, m->ns, m->d.use_bias, m->bimg, st);
             if (e != cudaSuccess) return cuda_fail(e, "build bf16 weight images");
         }
         return NNQS_OK;
@@ -413,6 +447,7 @@ int nnqs_log_psi(nnqs_model *m, const uint64_t *cfg, int64_t n, double *out, voi
         if (m->fp64) e = launch_log_psi(view<double>(m), cfg, n, out, m->nsm, st);
         else if (m->ns) e = launch_log_psi_tc(view<float>(m), m->bimg, m->pinv, m->ns, cfg, n, out, m->nsm, st);
         else e = launch_log_psi(view<float>(m), cfg, n, out, m->nsm, st);
+        if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 0, out, nullptr, st);
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "log_psi");
     });
 }
@@ -428,6 +463,7 @@ int nnqs_local_energy(nnqs_model *m, const uint64_t *cfg, int64_t n, double *elo
         if (int rc = check_cfg(m, cfg, n, st)) return rc;
         cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 0, eloc, nullptr, m->nsm, st)
                                 : launch_ratio(view<float>(m), cfg, n, 0, eloc, nullptr, m->nsm, st);
+        if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 1, eloc, nullptr, st);
         if (e != cudaSuccess) return cuda_fail(e, "local_energy");
         if (sums) {
             const int nb = 64;
@@ -463,6 +499,7 @@ int nnqs_lanczos_moments(nnqs_model *m, const uint64_t *cfg, int64_t n, double *
         double *H2 = h2 ? h2 : (double *)(ws + off_h2);
         cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, H1, H2, m->nsm, st)
                                 : launch_ratio(view<float>(m), cfg, n, 1, H1, H2, m->nsm, st);
+        if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 1, H1, H2, st);
         if (e != cudaSuccess) return cuda_fail(e, "lanczos");
         if (moments || lanczos) {
             e = launch_moments(H1, H2, n, (double *)ws, nb, moments, lanczos, st);
@@ -470,6 +507,47 @@ int nnqs_lanczos_moments(nnqs_model *m, const uint64_t *cfg, int64_t n, double *
         }
         return NNQS_OK;
     });
+}
+
+int nnqs_lanczos_partial(nnqs_model *m, const uint64_t *cfg, int64_t n, double *h1, double *h2, double *sums,
+                         void *stream)
+{
+    if (check_model(m)) return NNQS_EINVAL;
+    if (n < 0) return fail(NNQS_EINVAL, "n < 0");
+    if (!sums) return fail(NNQS_EINVAL, "sums_out must be non-NULL");
+    if (n > 0 && !cfg) return fail(NNQS_EINVAL, "cfg must be non-NULL");
+    return with_device(m, [&]() -> int {
+        cudaStream_t st = (cudaStream_t)stream;
+        if (n == 0) {
+            NNQS_CUDA(cudaMemsetAsync(sums, 0, kMomentSums * sizeof(double), st));
+            return NNQS_OK;
+        }
+        if (int rc = check_cfg(m, cfg, n, st)) return rc;
+        const int nb = 64;
+        size_t need = align256(nb * kMomentSums * sizeof(double));
+        const size_t off_h1 = need;
+        if (!h1) need += align256((size_t)n * 2 * sizeof(double));
+        const size_t off_h2 = need;
+        if (!h2) need += align256((size_t)n * 2 * sizeof(double));
+        int rc = ensure_ws(m, need);
+        if (rc) return rc;
+        char *ws = (char *)m->ws;
+        double *H1 = h1 ? h1 : (double *)(ws + off_h1);
+        double *H2 = h2 ? h2 : (double *)(ws + off_h2);
+        cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, H1, H2, m->nsm, st)
+                                : launch_ratio(view<float>(m), cfg, n, 1, H1, H2, m->nsm, st);
+        if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 1, H1, H2, st);
+        if (e == cudaSuccess) e = launch_moments(H1, H2, n, (double *)ws, nb, nullptr, nullptr, st, sums);
+        return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "lanczos_partial");
+    });
+}
+
+int nnqs_lanczos_finish(const double *sums, double *moments, double *lanczos, void *stream)
+{
+    if (!sums) return fail(NNQS_EINVAL, "sums must be non-NULL");
+    if (!moments && !lanczos) return NNQS_OK;
+    const cudaError_t e = launch_moments_finish(sums, moments, lanczos, (cudaStream_t)stream);
+    return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "lanczos_finish");
 }
 
 int nnqs_sample(nnqs_model *m, uint64_t seed, int32_t n_chains, int32_t n_per_chain, int32_t n_skip, int32_t n_burn,
@@ -627,6 +705,7 @@ int nnqs_lanczos_moments_noalloc(nnqs_model *m, const uint64_t *cfg, int64_t n, 
         if (int rc = check_cfg(m, cfg, n, st)) return rc;
         cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, h1, h2, m->nsm, st)
                                 : launch_ratio(view<float>(m), cfg, n, 1, h1, h2, m->nsm, st);
+        if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 1, h1, h2, st);
         if (e != cudaSuccess) return cuda_fail(e, "lanczos (fixed scratch)");
         if (moments || lanczos) {
             e = launch_moments(h1, h2, n, partial, kNoallocBlocks, moments, lanczos, st);
@@ -674,14 +753,17 @@ int nnqs_lanczos2(nnqs_model *m, const uint64_t *cfg, int64_t n, double *h3_out,
         if (T < 0 || T > tmax) return fail(NNQS_ECUDA, "neighbour count %lld out of range", (long long)T);
         auto log_psi = [&](const uint64_t *c, int64_t k, double *o) -> cudaError_t {
             if (k == 0) return cudaSuccess;
-            if (m->fp64) return launch_log_psi(view<double>(m), c, k, o, m->nsm, st);
-            if (m->ns) return launch_log_psi_tc(view<float>(m), m->bimg, m->pinv, m->ns, c, k, o, m->nsm, st);
-            return launch_log_psi(view<float>(m), c, k, o, m->nsm, st);
+            cudaError_t e2;
+            if (m->fp64) e2 = launch_log_psi(view<double>(m), c, k, o, m->nsm, st);
+            else if (m->ns) e2 = launch_log_psi_tc(view<float>(m), m->bimg, m->pinv, m->ns, c, k, o, m->nsm, st);
+            else e2 = launch_log_psi(view<float>(m), c, k, o, m->nsm, st);
+            return e2 == cudaSuccess ? mark_vanishing(m, c, k, 0, o, nullptr, st) : e2;
         };
         auto ratio = [&](const uint64_t *c, int64_t k, double *a, double *b) -> cudaError_t {
             if (k == 0) return cudaSuccess;
-            return m->fp64 ? launch_ratio(view<double>(m), c, k, 1, a, b, m->nsm, st)
-                           : launch_ratio(view<float>(m), c, k, 1, a, b, m->nsm, st);
+            const cudaError_t e2 = m->fp64 ? launch_ratio(view<double>(m), c, k, 1, a, b, m->nsm, st)
+                                           : launch_ratio(view<float>(m), c, k, 1, a, b, m->nsm, st);
+            return e2 == cudaSuccess ? mark_vanishing(m, c, k, 1, a, b, st) : e2;
         };
         e = m->fp64 ? launch_fill_nb(view<double>(m), cfg, n, off, ncfg, ncoef, st)
                     : launch_fill_nb(view<float>(m), cfg, n, off, ncfg, ncoef, st);
@@ -735,6 +817,7 @@ int nnqs_status(nnqs_model *m, void *stream)
         NNQS_CUDA(cudaStreamSynchronize(st));
         NNQS_CUDA(cudaMemcpy(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost));
         NNQS_CUDA(cudaMemset(m->status, 0, sizeof(int)));
+        if (h == NNQS_ETIMEOUT) return fail(h, "a bounded device-side wait ran out (the kernel returned early)");
         if (h) return fail(h, "a kernel produced a non-finite amplitude");
         return NNQS_OK;
     });

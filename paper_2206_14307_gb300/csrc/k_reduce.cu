@@ -84,14 +84,76 @@ cudaError_t launch_check_sz0(const uint64_t *cfg, int64_t n, int nwords, int N, 
     return cudaGetLastError();
 }
 
-// stage 2: fixed-order sum of the partials, moments and the p = 1 Lanczos step
+// Configurations whose projected amplitude vanishes identically (Eqs. 4-6): s is
+// fixed by an operation g with chi(g) = -1 (T_g s = s), or mapped to -s by g
+// where the inverted term's character is -1 (chi_P chi(g) with spin inversion;
+// chi(g) for bias-free RBMs without inversion, which are even in s).  Then
+// psi(s) = -psi(s) = 0 exactly, whatever the rounding of the sum.  One warp per
+// configuration, lanes over g.  mode 0: o1[k] = log psi = (-inf, 0); mode 1
+// (E_loc, h1, h2 = 0/0): o1[k], o2[k] = NaN and NNQS_ERANGE in the status word.
+template <typename T>
+__global__ void k_mark_vanishing(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n, int mode,
+                                 double *__restrict__ o1, double *__restrict__ o2)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int inv_char = md.nsign == 2 ? md.chiP : (md.use_bias ? 0 : 1);
+    for (int64_t k = wid; k < n; k += nw) {
+        const uint64_t *w = cfg + k * md.nwords;
+        bool dead = false;
+        for (int g = lane; g < md.G && !dead; g += 32) {
+            const T chi = md.chi[g];
+            bool fix = chi < T(0), flip = (double)inv_char * (double)chi < 0.0;
+            const uint8_t *pg = md.perm + (size_t)g * md.N;
+            for (int i = 0; i < md.N && (fix || flip); ++i) {
+                const int a = spin_of(w, i), b = spin_of(w, pg[i]);
+                if (a != b) fix = false;
+                if (a != -b) flip = false;
+            }
+            dead = fix || flip;
+        }
+        if (__any_sync(0xffffffffu, dead) && lane == 0) {
+            if (mode == 0) {
+                o1[2 * k] = -INFINITY;
+                o1[2 * k + 1] = 0.0;
+            } else {
+                flag_range(md.status);
+                if (o1) { o1[2 * k] = nan(""); o1[2 * k + 1] = nan(""); }
+                if (o2) { o2[2 * k] = nan(""); o2[2 * k + 1] = nan(""); }
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_mark_vanishing(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int mode, double *o1,
+                                  double *o2, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 7) / 8;
+    const int grid = (int)(want < 2048 ? want : 2048);
+    k_mark_vanishing<T><<<grid, 256, 0, st>>>(md, cfg, n, mode, o1, o2);
+    return cudaGetLastError();
+}
+template cudaError_t launch_mark_vanishing<float>(const DevModel<float> &, const uint64_t *, int64_t, int, double *,
+                                                  double *, cudaStream_t);
+template cudaError_t launch_mark_vanishing<double>(const DevModel<double> &, const uint64_t *, int64_t, int,
+                                                   double *, double *, cudaStream_t);
+
+// stage 2: fixed-order sum of the partials (raw sums to sums_out), moments and
+// the p = 1 Lanczos step; with nb = 1 and partial = the all-reduced raw sums of
+// several processes it is the finishing step of a distributed Lanczos step
 __global__ void __launch_bounds__(32) k_moments_final(const double *__restrict__ partial, int nb,
-                                                      double *__restrict__ moments, double *__restrict__ lanczos)
+                                                      double *__restrict__ sums_out, double *__restrict__ moments,
+                                                      double *__restrict__ lanczos)
 {
     if (threadIdx.x != 0) return;
     double v[kMomentSums] = {0, 0, 0, 0, 0, 0, 0};
     for (int b = 0; b < nb; ++b)
         for (int q = 0; q < kMomentSums; ++q) v[q] += partial[b * kMomentSums + q];
+    if (sums_out)
+        for (int q = 0; q < kMomentSums; ++q) sums_out[q] = v[q];
     const double z = v[0] > 0 ? v[0] : 1.0;
     const double m1 = v[1] / z, m2 = v[2] / z, m3 = v[3] / z;
     if (moments) {
@@ -102,10 +164,16 @@ __global__ void __launch_bounds__(32) k_moments_final(const double *__restrict__
 }
 
 cudaError_t launch_moments(const double *h1, const double *h2, int64_t n, double *partial, int nblocks,
-                           double *moments, double *lanczos, cudaStream_t st)
+                           double *moments, double *lanczos, cudaStream_t st, double *sums_out)
 {
     k_moments_partial<<<nblocks, kRedThreads, 0, st>>>(h1, h2, n, partial);
-    k_moments_final<<<1, 32, 0, st>>>(partial, nblocks, moments, lanczos);
+    k_moments_final<<<1, 32, 0, st>>>(partial, nblocks, sums_out, moments, lanczos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_finish(const double *sums, double *moments, double *lanczos, cudaStream_t st)
+{
+    k_moments_final<<<1, 32, 0, st>>>(sums, 1, nullptr, moments, lanczos);
     return cudaGetLastError();
 }
 

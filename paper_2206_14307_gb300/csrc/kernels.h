@@ -83,14 +83,23 @@ template <typename T>
 cudaError_t launch_grad(const DevModel<T> &md, const uint64_t *cfg, int64_t n, double *O, void *scratch, int grid,
                         cudaStream_t st);
 
+// configurations annihilated by the projection: mode 0 sets log psi = -inf,
+// mode 1 sets h1/h2 (either may be NULL) to NaN and flags NNQS_ERANGE
+template <typename T>
+cudaError_t launch_mark_vanishing(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int mode, double *o1,
+                                  double *o2, cudaStream_t st);
+
 // checked mode: first_bad <- lowest index of a configuration outside Sz = 0
 // (UINT64_MAX if none)
 cudaError_t launch_check_sz0(const uint64_t *cfg, int64_t n, int nwords, int N, unsigned long long *first_bad,
                              cudaStream_t st);
 
-// FP64 reductions
+// FP64 reductions.  launch_moments: per-block partials -> raw sums (sums_out
+// [kMomentSums], may be NULL), moments and the p = 1 step; launch_moments_finish:
+// moments and the p = 1 step from raw sums (e.g. summed over processes).
 cudaError_t launch_moments(const double *h1, const double *h2, int64_t n, double *partial, int nblocks,
-                           double *moments, double *lanczos, cudaStream_t st);
+                           double *moments, double *lanczos, cudaStream_t st, double *sums_out = nullptr);
+cudaError_t launch_moments_finish(const double *sums, double *moments, double *lanczos, cudaStream_t st);
 cudaError_t launch_eloc_sums(const double *eloc, int64_t n, double *partial, int nblocks, double *sums,
                              cudaStream_t st);
 // SR pieces (Eq. 12), all in FP64; weights may be NULL (plain sample means)
@@ -113,11 +122,16 @@ cudaError_t launch_tables_conn(const double *params, int N, int M, int Mp, int K
                                const int16_t *bi, const int16_t *bj, cx<T> *Tb, cx<T> *Cb, cx<T> *S4, cx<T> *CS,
                                sc<T> *ES, cudaStream_t st);
 
-// tensor-core (tcgen05) log psi with BF16-split weights: NS = 2 or 3 terms
+// tensor-core (tcgen05) log psi with BF16-split weights: NS = 2 or 3 terms.
+// The device image (tc_bimg_bytes) holds the split weights of every (RBM,
+// hidden tile) and the bias table; pinv is [G][round16(N)] uint16 (tc_pinv_table).
 bool tc_supported(int N, int M, int G, int K, int nsign, int NS);
-size_t tc_bimg_bytes(int N, int M, int K, int NS);
-cudaError_t launch_bimg(const double *params, int N, int M, int K, int NS, uint16_t *img, cudaStream_t st);
-cudaError_t launch_log_psi_tc(const DevModel<float> &md, const uint16_t *bimg, const uint8_t *pinv, int NS,
+size_t tc_bimg_bytes(int N, int M, int G, int K, int nsign, int NS);
+size_t tc_pinv_bytes(int N, int G);
+void tc_pinv_table(const uint8_t *perm, int N, int G, uint16_t *out);
+cudaError_t launch_bimg(const double *params, int N, int M, int G, int K, int nsign, int NS, int use_bias,
+                        uint16_t *img, cudaStream_t st);
+cudaError_t launch_log_psi_tc(const DevModel<float> &md, const uint16_t *bimg, const uint16_t *pinv, int NS,
                               const uint64_t *cfg, int64_t n, double *out, int nsm, cudaStream_t st);
 
 }  // namespace nnqs

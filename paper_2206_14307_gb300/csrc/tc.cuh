@@ -34,12 +34,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
         : "memory");
     return ok != 0;
 }
-// Waits for the phase with an iteration limit; returns false if it ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint32_t max_iter = 1u << 22)
+__device__ __forceinline__ uint64_t globaltimer_ns()
 {
-    for (uint32_t it = 0; it < max_iter; ++it)
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the phase for at most limit_ns nanoseconds of wall time (about two
+// seconds by default: every legitimate wait here is microseconds long);
+// returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint64_t limit_ns = 2000000000ull)
+{
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, phase)) return true;
-    return false;
+        if ((it & 31u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
+    }
 }
 
 // ---- bulk copy global -> shared (TMA engine), completes on an mbarrier ------
@@ -84,7 +95,29 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 2 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &v0, float &v1)
+{
+    uint32_t r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr) : "memory");
+    v0 = __uint_as_float(r0);
+    v1 = __uint_as_float(r1);
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- named barrier over a subset of the CTA's warps ---------------------------
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ---- hardware 2^x (MUFU; relative error about 2^-22, flushes denormals) -------
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // ---- MMA ----------------------------------------------------------------------
 // D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 inputs, fp32 accumulator), issued by one thread.

@@ -31,7 +31,7 @@ ABI_FUNCTIONS = (
     "nnqs_num_tile_shapes", "nnqs_tile_shape", "nnqs_batch_create", "nnqs_batch_destroy", "nnqs_batch_size",
     "nnqs_batch_model", "nnqs_batch_get_shape", "nnqs_batch_set_shape", "nnqs_batch_autotune",
     "nnqs_batch_lanczos", "nnqs_batch_status", "nnqs_lanczos_variance", "nnqs_structure_factor",
-    "nnqs_lanczos2",
+    "nnqs_lanczos2", "nnqs_lanczos_partial", "nnqs_lanczos_finish",
 )
 NOALLOC_MAX_SAMPLES = 65536
 
@@ -83,6 +83,8 @@ def lib():
             "nnqs_last_error": ([], ctypes.c_char_p),
             "nnqs_lanczos_variance": ([P, P, P, P], ctypes.c_int),
             "nnqs_lanczos2": ([P, P, i64, P, P, P, P], ctypes.c_int),
+            "nnqs_lanczos_partial": ([P, P, i64, P, P, P, P], ctypes.c_int),
+            "nnqs_lanczos_finish": ([P, P, P, P], ctypes.c_int),
             "nnqs_structure_factor": ([P, P, i64, P, P, P], ctypes.c_int),
             "nnqs_num_tile_shapes": ([], i32),
             "nnqs_tile_shape": ([i32, P, P], ctypes.c_int),
@@ -157,6 +159,14 @@ def nnqs_lanczos_moments_noalloc(h, cfg, n, moments, lanczos, stream=0):
 
 def nnqs_lanczos2(h, cfg, n, h3, mu, out, stream=0):
     return _check(lib().nnqs_lanczos2(h, cfg, n, h3, mu, out, stream))
+
+
+def nnqs_lanczos_partial(h, cfg, n, h1, h2, sums, stream=0):
+    return _check(lib().nnqs_lanczos_partial(h, cfg, n, h1, h2, sums, stream))
+
+
+def nnqs_lanczos_finish(sums, moments, lanczos, stream=0):
+    return _check(lib().nnqs_lanczos_finish(sums, moments, lanczos, stream))
 
 
 def nnqs_lanczos_variance(moments, lanczos, out, stream=0):
@@ -284,6 +294,14 @@ class Model:
                              lanczos.data_ptr(), _stream())
         return h1, h2, moments, lanczos
 
+    def lanczos_partial(self, cfg, h1=None, h2=None, sums=None):
+        """This process's h1, h2 and raw FP64 sums [7] (see lanczos_finish)."""
+        n = cfg.shape[0]
+        sums = self._out(7) if sums is None else sums
+        nnqs_lanczos_partial(self.h, cfg.data_ptr() if n else None, n, _ptr(h1), _ptr(h2), sums.data_ptr(),
+                             _stream())
+        return h1, h2, sums
+
     def sample(self, seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out=None, acc_out=None):
         import torch
         if cfg_out is None:
@@ -338,6 +356,36 @@ class Model:
 
     def status(self):
         return nnqs_status(self.h, _stream())
+
+
+def lanczos_finish(sums, moments=None, lanczos=None):
+    """Moments [8] and the p = 1 step [3] from raw sums [7] summed over processes."""
+    import torch
+    moments = torch.empty(8, dtype=torch.float64, device=sums.device) if moments is None else moments
+    lanczos = torch.empty(3, dtype=torch.float64, device=sums.device) if lanczos is None else lanczos
+    nnqs_lanczos_finish(sums.data_ptr(), moments.data_ptr(), lanczos.data_ptr(), _stream())
+    return moments, lanczos
+
+
+def allreduce_sums(sums, group=None):
+    """Element-wise sum of a raw-sum tensor over the processes of a
+    torch.distributed group (in place; a no-op without an initialised group
+    of more than one process).  This is the one exchange step of the
+    distributed Lanczos step: 7 doubles per process."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
+    return sums
+
+
+def lanczos_distributed(model, cfg, h1=None, h2=None, group=None):
+    """One Lanczos step over the union of every process's samples: the
+    partial sums of this process's cfg, their all-reduce, the closed form.
+    Returns (sums, moments, lanczos) on this process's device."""
+    _, _, sums = model.lanczos_partial(cfg, h1, h2)
+    allreduce_sums(sums, group)
+    moments, lanczos = lanczos_finish(sums)
+    return sums, moments, lanczos
 
 
 def lanczos_variance(moments, lanczos, out=None):
