@@ -1,0 +1,7 @@
+// Tensor-core log psi with 16 hidden units per epilogue thread and block (one
+// translation unit per unit count, so that the variants compile in parallel).
+#include "k_logpsi_tc.cuh"
+
+namespace nnqs {
+NNQS_TC_INSTANTIATE(16)
+}  // namespace nnqs
