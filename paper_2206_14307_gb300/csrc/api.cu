@@ -561,6 +561,13 @@ int nnqs_sample(nnqs_model *m, uint64_t seed, int32_t n_chains, int32_t n_per_ch
         return fail(NNQS_EINVAL, "total number of steps exceeds 2^31 - 1");
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
+        if (!m->fp64) {
+            // the chain caches in the shared memory of thread-block clusters, when they fit
+            cudaError_t e = cudaSuccess;
+            if (launch_sample_cl(view<float>(m), seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, m->nsm,
+                                 st, &e))
+                return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "sample (cluster)");
+        }
         const size_t per = m->fp64 ? sampler_cache_bytes(view<double>(m)) : sampler_cache_bytes(view<float>(m));
         const int conc = m->fp64 ? sampler_grid(view<double>(m), n_chains, m->nsm) : sampler_grid(view<float>(m), n_chains, m->nsm);
         (void)conc;

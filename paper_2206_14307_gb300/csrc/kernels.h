@@ -74,6 +74,11 @@ template <typename T> int sampler_grid(const DevModel<T> &md, int n_chains, int 
 template <typename T>
 cudaError_t launch_sample(const DevModel<T> &md, uint64_t seed, int n_chains, int n_per_chain, int n_skip, int n_burn,
                           uint64_t *cfg_out, float *acc_out, void *cache, int nsm, cudaStream_t st);
+// FP32 sampler with each chain's cache in the shared memory of a thread-block
+// cluster; returns false (launching nothing) when the cache does not fit a
+// cluster of at most 8 CTAs, else the launch status in *err.
+bool launch_sample_cl(const DevModel<float> &md, uint64_t seed, int n_chains, int n_per_chain, int n_skip, int n_burn,
+                      uint64_t *cfg_out, float *acc_out, int nsm, cudaStream_t st, cudaError_t *err);
 
 // Per-CTA scratch of the gradient kernel (U, V rows) and its grid size.
 template <typename T> size_t grad_scratch_bytes(const DevModel<T> &md);
