@@ -131,6 +131,7 @@ struct nnqs_model {
     uint16_t *pinv = nullptr;    // inverse permutations [G][round16(N)]
     int *status = nullptr;
     unsigned long long *chk = nullptr;  // checked mode: first configuration outside Sz = 0
+    void *eft = nullptr;                // FP32 E_loc: paired per-bond tables (nullptr: not supported)
     void *ws = nullptr;
     size_t ws_bytes = 0;
 };
@@ -153,6 +154,15 @@ template <typename T> DevModel<T> view(const nnqs_model *m)
     v.ES = (const sc<T> *)m->ES;
     v.status = m->status;
     return v;
+}
+
+// Test hook: NNQS_TEST_ELOC_ENGINE=old runs E_loc on the general connected-
+// configuration engine even where the shared-memory form applies (for
+// comparisons of the two).  Unset in normal use.
+bool test_old_engine()
+{
+    const char *v = getenv("NNQS_TEST_ELOC_ENGINE");
+    return v && v[0] == 'o';
 }
 
 // Test hook: NNQS_TEST_WORKSPACE_CAP=<bytes> makes every workspace growth
@@ -318,6 +328,11 @@ static int create_model(const nnqs_desc *desc, int mp_min, nnqs_model **out)
     ALLOC(m->bperm, (size_t)m->G * bi.size() * sizeof(uint16_t));
     ALLOC(m->status, sizeof(int));
     ALLOC(m->chk, sizeof(unsigned long long));
+    if (!m->fp64) {
+        DevModel<float> v{};
+        v.K = d.K; v.M = d.M; v.N = m->N; v.G = m->G; v.nbonds = (int)bi.size(); v.Mp = m->Mp;
+        if (eloc_fast_supported(v)) ALLOC(m->eft, eloc_fast_table_bytes(v));
+    }
     if (d.precision == NNQS_BF16X2 || d.precision == NNQS_BF16X3) {
         const int ns = d.precision == NNQS_BF16X2 ? 2 : 3;
         if (tc_supported((int)N, d.M, m->G, d.K, m->nsign, ns)) {
@@ -375,7 +390,7 @@ int nnqs_destroy(nnqs_model *m)
     if (!m) return NNQS_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {m->perm, m->bi, m->bj, m->bt, m->chi, m->params, m->Wt, m->b, m->a, m->logc, m->X, m->XA,
-                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->chk, m->ws, m->bimg, m->pinv};
+                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->chk, m->eft, m->ws, m->bimg, m->pinv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -413,6 +428,10 @@ int nnqs_set_params_device(nnqs_model *m, const double *params, int64_t P, void 
                                           (cx<float> *)m->Tb, (cx<float> *)m->Cb, (cx<float> *)m->S4,
                                           (cx<float> *)m->CS, (sc<float> *)m->ES, st);
         if (e != cudaSuccess) return cuda_fail(e, "build connection tables");
+        if (m->eft) {
+            e = launch_tables_paired(view<float>(m), m->eft, st);
+            if (e != cudaSuccess) return cuda_fail(e, "build paired tables");
+        }
         if (m->ns) {
             e = launch_bimg(m->params, m->N, m->d.M, m->G, m->d.K, m->nsign, m->ns, m->d.use_bias, m->bimg, st);
             if (e != cudaSuccess) return cuda_fail(e, "build bf16 weight images");
@@ -461,8 +480,10 @@ int nnqs_local_energy(nnqs_model *m, const uint64_t *cfg, int64_t n, double *elo
     return with_device(m, [&]() -> int {
         cudaStream_t st = (cudaStream_t)stream;
         if (int rc = check_cfg(m, cfg, n, st)) return rc;
-        cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 0, eloc, nullptr, m->nsm, st)
-                                : launch_ratio(view<float>(m), cfg, n, 0, eloc, nullptr, m->nsm, st);
+        cudaError_t e;
+        if (m->fp64) e = launch_ratio(view<double>(m), cfg, n, 0, eloc, nullptr, m->nsm, st);
+        else if (m->eft && !test_old_engine()) e = launch_eloc_fast(view<float>(m), m->eft, cfg, n, eloc, m->nsm, st);
+        else e = launch_ratio(view<float>(m), cfg, n, 0, eloc, nullptr, m->nsm, st);
         if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 1, eloc, nullptr, st);
         if (e != cudaSuccess) return cuda_fail(e, "local_energy");
         if (sums) {

@@ -1,0 +1,462 @@
+// k_eloc_fast.cu -- E_loc (Eq. 10) in FP32 with the per-bond tables in shared
+// memory and packed f32x2 arithmetic.
+//
+// For a sample s, a row t = (r, g, sign) of the projected sum (Eqs. 4-6) with
+// p_m = e^{theta_m}/(2cosh theta_m), and an anti-aligned bond b, the row's ratio
+// is e^{C} prod_m (1 + p_m T_m): T = e^{2 Delta} - 1 and the prefactor exponent
+// C belong to the bond's image b' = g(b) and its orientation (the tables of the
+// connected-configuration engine).  Then
+//   E_loc = diag(s) + sum_b (J_b/2) [sum_t w_t ratio_{t,b}] / [sum_t w_t],
+// w_t = c_r chi(g) chi_P e^{+-a.T_g s} prod_m 2cosh(theta_m) the row's term.
+//
+// Layout: one CTA per SM (the tables of one model, 2 x 4N rows per RBM, are
+// copied into its shared memory once), one sample at a time.  A group of 8
+// lanes owns a row; lane l owns the unit pairs k = l + 8 j (units 2k, 2k + 1),
+// whose p sit in registers as packed pairs.  The table row of a bond image is
+// stored as float4 (Tx_2k, Tx_2k+1, Ty_2k, Ty_2k+1) per pair, so a group reads
+// one contiguous 128-byte row segment per step (conflict-free) and
+// (1 + p T) and the running products of the even and odd units are packed
+// FP32x2 operations.  Entries (anti-aligned bonds) go 8 at a time: lane l
+// decodes entry l (image bond, orientation, prefactor) and the group shares
+// the table offsets by shuffle; a butterfly product-reduce-scatter over the
+// group leaves lane l with entry l's full product, which it weights by the
+// prefactor and the row term and adds into the warp's sum for that entry.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nnqs {
+
+constexpr int kEfGL = 8;                 // lanes per row group
+constexpr int kEfMaxThreads = 512;   // at most 16 warps (128 registers per thread)
+
+// ---- packed FP32 pairs ------------------------------------------------------
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float lo, float hi)
+{
+    return (f2)__float_as_uint(lo) | ((f2)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2_lo(f2 v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(f2 v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// one 128-bit shared-memory load as two packed pairs
+__device__ __forceinline__ void lds128(const void *p, f2 &a, f2 &b)
+{
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+struct EfArgs {
+    const float4 *tp;     // [K][2][NB][MH] paired per-bond tables T
+    const sc<float> *ep;  // [K][2][NB] e^{+C}, e^{-C}
+    int MH;               // unit pairs per table row (8 NP)
+    int warps;
+};
+
+// scaled product of two scaled complex numbers, unnormalised exponents kept exact
+__device__ __forceinline__ void scm(float &x, float &y, int &e, float x2, float y2, int e2)
+{
+    const float nx = x * x2 - y * y2, ny = x * y2 + y * x2;
+    x = nx; y = ny; e += e2;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kEfMaxThreads, 1)
+    k_eloc_fast(DevModel<float> md, EfArgs ea, const uint64_t *__restrict__ cfg, int64_t n, double *__restrict__ h1_out)
+{
+    constexpr int NG = 32 / kEfGL;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int NB = md.nbonds, K = md.K, MH = ea.MH, N = md.N, M = md.M;
+    float4 *tps = reinterpret_cast<float4 *>(smem);                                      // [K][2][NB][MH]
+    sc<float> *eps = reinterpret_cast<sc<float> *>(tps + (size_t)K * 2 * NB * MH);      // [K][2][NB]
+    sc<float> *acc = eps + (size_t)K * 2 * NB;                                          // [warps][NB]
+    __shared__ float s_sm[kMaxN];
+    __shared__ int8_t s8[kMaxN];
+    __shared__ uint16_t aa[4 * kMaxN];   // anti-aligned bond | (s_i > 0) << 15
+    __shared__ int n_aa;
+    __shared__ float diag_sh;
+    __shared__ sc<float> wsum[32];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int grp = lane / kEfGL, gl = lane % kEfGL;
+    const int gidx = warp * NG + grp, ngroups = nwarps * NG;
+
+    // tables into shared memory (once per CTA)
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(ea.tp);
+        int4 *dst = reinterpret_cast<int4 *>(tps);
+        for (int q = threadIdx.x; q < K * 2 * NB * MH; q += blockDim.x) dst[q] = src[q];
+        for (int q = threadIdx.x; q < K * 2 * NB; q += blockDim.x) eps[q] = ea.ep[q];
+    }
+
+    for (int64_t smp = blockIdx.x; smp < n; smp += gridDim.x) {
+        const uint64_t *w = cfg + smp * md.nwords;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int sv = spin_of(w, i);
+            s_sm[i] = (float)sv;
+            s8[i] = (int8_t)sv;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            float d = 0.f;
+            int base = 0;
+            for (int b0 = 0; b0 < NB; b0 += 32) {
+                const int b = b0 + lane;
+                bool isaa = false;
+                int si = 0;
+                if (b < NB) {
+                    si = s8[md.bond_i[b]];
+                    const int sj = s8[md.bond_j[b]];
+                    d += 0.25f * bondJ(md, b) * (float)(si * sj);
+                    isaa = si != sj;
+                }
+                const unsigned bm = __ballot_sync(0xffffffffu, isaa);
+                if (isaa) aa[base + __popc(bm & ((1u << lane) - 1u))] = (uint16_t)(b | (si > 0 ? 0x8000 : 0));
+                base += __popc(bm);
+            }
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (lane == 0) { n_aa = base; diag_sh = d; }
+        }
+        __syncthreads();
+        const int naa = n_aa;
+        for (int q = threadIdx.x; q < nwarps * naa; q += blockDim.x) {
+            const int wq = q / naa, e = q - wq * naa;
+            acc[wq * NB + e] = sc<float>{0.f, 0.f, 0};
+        }
+        sc<float> s0acc{0.f, 0.f, 0};   // this group's sum of row terms (lane 0 of the group)
+        __syncthreads();
+
+        // (every group of a warp takes the same number of rows, so that the
+        // warp-wide shuffles below see all lanes; groups past the last row
+        // compute row 0 and add nothing)
+        for (int rbase = 0; rbase < K * md.G; rbase += ngroups) {
+            const bool active = rbase + gidx < K * md.G;
+            const int row = active ? rbase + gidx : 0;
+            const int r = row / md.G, g = row - r * md.G;
+            const uint8_t *pg = md.perm + (size_t)g * N;
+            // ---- theta' = W_r T_g s for the lane's units (pairs k = gl + 8 j) ----
+            float tx[2 * NP], ty[2 * NP];
+#pragma unroll
+            for (int u = 0; u < 2 * NP; ++u) { tx[u] = 0.f; ty[u] = 0.f; }
+            const cx<float> *Wr = md.Wt + (size_t)r * N * M;
+            for (int i = 0; i < N; ++i) {
+                const cx<float> *wk = Wr + (size_t)pg[i] * M;
+                const float si = s_sm[i];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const int m = 2 * (gl + kEfGL * j);
+                    if ((M & 1) == 0 && m + 1 < M) {   // M even: both units of the pair, one aligned 16-byte load
+                        const float4 a = *reinterpret_cast<const float4 *>(wk + m);
+                        tx[2 * j] = fmaf(si, a.x, tx[2 * j]); ty[2 * j] = fmaf(si, a.y, ty[2 * j]);
+                        tx[2 * j + 1] = fmaf(si, a.z, tx[2 * j + 1]); ty[2 * j + 1] = fmaf(si, a.w, ty[2 * j + 1]);
+                    } else {
+                        if (m < M) { const cx<float> a = wk[m]; tx[2 * j] = fmaf(si, a.x, tx[2 * j]); ty[2 * j] = fmaf(si, a.y, ty[2 * j]); }
+                        if (m + 1 < M) { const cx<float> a = wk[m + 1]; tx[2 * j + 1] = fmaf(si, a.x, tx[2 * j + 1]); ty[2 * j + 1] = fmaf(si, a.y, ty[2 * j + 1]); }
+                    }
+                }
+            }
+            cx<float> at{0.f, 0.f};
+            if (md.use_bias) {
+                const cx<float> *ar = md.avec + (size_t)r * N;
+                for (int i = gl; i < N; i += kEfGL) { const cx<float> a = ar[pg[i]]; at.x += s_sm[i] * a.x; at.y += s_sm[i] * a.y; }
+#pragma unroll
+                for (int o = kEfGL / 2; o > 0; o >>= 1) {
+                    at.x += __shfl_xor_sync(0xffffffffu, at.x, o);
+                    at.y += __shfl_xor_sync(0xffffffffu, at.y, o);
+                }
+            }
+            for (int sg = 0; sg < md.nsign; ++sg) {
+                const float sign = sg ? -1.f : 1.f;
+                // ---- p of the lane's units (packed pairs) and the row term ----
+                f2 px[NP], py[NP], npy[NP];
+                sc<float> prod{1.f, 0.f, 0};
+                const cx<float> *br = md.bvec + (size_t)r * M;
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    float pxv[2], pyv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int m = 2 * (gl + kEfGL * j) + h;
+                        pxv[h] = 0.f; pyv[h] = 0.f;
+                        if (m < M) {
+                            cx<float> th{sign * tx[2 * j + h], sign * ty[2 * j + h]};
+                            if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
+                            cx<float> mant, pv;
+                            int k;
+                            cosh2(th, mant, k, pv);
+                            pxv[h] = pv.x; pyv[h] = pv.y;
+                            const cx<float> q = cmul(mk(prod.x, prod.y), mant);
+                            prod = sc<float>{q.x, q.y, prod.e + k};
+                        }
+                    }
+                    px[j] = f2_pack(pxv[0], pxv[1]);
+                    py[j] = f2_pack(pyv[0], pyv[1]);
+                    npy[j] = f2_pack(-pyv[0], -pyv[1]);
+                }
+                prod = sc_norm(prod);
+#pragma unroll
+                for (int o = kEfGL / 2; o > 0; o >>= 1) {
+                    const sc<float> v{__shfl_xor_sync(0xffffffffu, prod.x, o), __shfl_xor_sync(0xffffffffu, prod.y, o),
+                                      __shfl_xor_sync(0xffffffffu, prod.e, o)};
+                    prod = sc_mul(prod, v);
+                }
+                const cx<float> lc = md.logc[r];
+                sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
+                float c = md.chi[g];
+                if (sg && md.chiP < 0) c = -c;
+                lead.x *= c; lead.y *= c;
+                const sc<float> wt = sc_mul(prod, sc_norm(lead));   // the row term (same in every lane)
+                if (gl == 0 && active) s0acc = sc_add(s0acc, wt);
+
+                const f2 one2 = f2_pack(1.f, 1.f);
+                // ---- entries, 8 at a time ----
+                for (int e0 = 0; e0 < naa; e0 += kEfGL) {
+                    // lane gl: table offset and prefactor of entry e0 + gl
+                    const int e = e0 + gl;
+                    int off = 0;
+                    sc<float> pre{0.f, 0.f, 0};
+                    if (e < naa) {
+                        const uint16_t code = aa[e];
+                        const int b = code & 0x7fff;
+                        const uint16_t bp = md.bperm[(size_t)g * NB + b];
+                        const int bb = bp & 0x7fff;
+                        // orientation of the exchange on the image bond, for this sign
+                        const bool pos = ((code >> 15) != 0) != ((bp >> 15) != 0);   // s_i flip-corrected
+                        const int o = (pos != (sg != 0)) ? 0 : 1;
+                        off = ((r * 2 + o) * NB + bb) * MH;
+                        pre = eps[(r * 2 + o) * NB + bb];
+                    }
+                    float rx[kEfGL], ry[kEfGL];
+                    int re[kEfGL];
+#pragma unroll
+                    for (int q = 0; q < kEfGL; ++q) {
+                        const int oq = __shfl_sync(0xffffffffu, off, grp * kEfGL + q);
+                        const float4 *trow = tps + oq;
+                        // running products of the even and odd units (packed)
+                        f2 Rx = one2, Ry = 0;
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) {
+                            f2 tx2, ty2;
+                            lds128(trow + gl + kEfGL * j, tx2, ty2);
+                            const f2 fx = fma2(npy[j], ty2, fma2(px[j], tx2, one2));   // 1 + px tx - py ty
+                            const f2 fy = fma2(py[j], tx2, mul2(px[j], ty2));           // px ty + py tx
+                            if (j == 0) {
+                                Rx = fx; Ry = fy;
+                            } else {
+                                const f2 nx = sub2(mul2(Rx, fx), mul2(Ry, fy));
+                                Ry = fma2(Rx, fy, mul2(Ry, fx));
+                                Rx = nx;
+                            }
+                        }
+                        // even x odd, then mantissa / exponent
+                        float x = f2_lo(Rx) * f2_hi(Rx) - f2_lo(Ry) * f2_hi(Ry);
+                        float y = f2_lo(Rx) * f2_hi(Ry) + f2_lo(Ry) * f2_hi(Rx);
+                        const int ex = expo<float>(x, y);
+                        const float s = pow2i<float>(-ex);
+                        rx[q] = x * s; ry[q] = y * s; re[q] = ex;
+                    }
+                    // butterfly product-reduce-scatter: lane gl ends with entry gl's product
+#pragma unroll
+                    for (int lev = 0; lev < 3; ++lev) {
+                        const int o = 4 >> lev;          // lane distance 4, 2, 1
+                        const int cnt = 4 >> lev;        // entries exchanged
+                        const bool upper = (gl & o) != 0;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (q < cnt) {
+                                // keep slot q (lower lanes keep the low half), send the other
+                                const float sx = upper ? rx[q] : rx[q + cnt];
+                                const float sy = upper ? ry[q] : ry[q + cnt];
+                                const int se = upper ? re[q] : re[q + cnt];
+                                const float kx = upper ? rx[q + cnt] : rx[q];
+                                const float ky = upper ? ry[q + cnt] : ry[q];
+                                const int ke = upper ? re[q + cnt] : re[q];
+                                const float gx = __shfl_xor_sync(0xffffffffu, sx, o);
+                                const float gy = __shfl_xor_sync(0xffffffffu, sy, o);
+                                const int ge = __shfl_xor_sync(0xffffffffu, se, o);
+                                float nx = kx, ny = ky;
+                                int ne = ke;
+                                scm(nx, ny, ne, gx, gy, ge);
+                                rx[q] = nx; ry[q] = ny; re[q] = ne;
+                            }
+                        }
+                    }
+                    // lane gl: entry e0 + gl (the kept slot 0), times prefactor and row term
+                    sc<float> v{0.f, 0.f, 0};
+                    if (e < naa && active) v = sc_mul(sc_mul(sc_norm(sc<float>{rx[0], ry[0], re[0]}), pre), wt);
+                    // sum over the warp's groups (they hold the same entries), then into the warp's sums
+#pragma unroll
+                    for (int o = kEfGL; o < 32; o <<= 1) {
+                        const sc<float> u{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
+                                          __shfl_xor_sync(0xffffffffu, v.e, o)};
+                        v = sc_add(v, u);
+                    }
+                    if (grp == 0 && e < naa) acc[warp * NB + e] = sc_add(acc[warp * NB + e], v);
+                }
+            }
+        }
+        // ---- the sum of all row terms (lane 0 of each group holds its part) ----
+#pragma unroll
+        for (int o = kEfGL; o < 32; o <<= 1) {
+            const sc<float> u{__shfl_xor_sync(0xffffffffu, s0acc.x, o), __shfl_xor_sync(0xffffffffu, s0acc.y, o),
+                              __shfl_xor_sync(0xffffffffu, s0acc.e, o)};
+            s0acc = sc_add(s0acc, u);
+        }
+        if (lane == 0) wsum[warp] = s0acc;
+        __syncthreads();
+        if (warp == 0) {
+            sc<float> tot{0.f, 0.f, 0};
+            if (lane == 0)
+                for (int q = 0; q < nwarps; ++q) tot = sc_add(tot, wsum[q]);
+            const sc<float> S0{__shfl_sync(0xffffffffu, tot.x, 0), __shfl_sync(0xffffffffu, tot.y, 0),
+                               __shfl_sync(0xffffffffu, tot.e, 0)};
+            double hx = 0.0, hy = 0.0;
+            for (int e = lane; e < naa; e += 32) {
+                sc<float> se = acc[e];
+                for (int q = 1; q < nwarps; ++q) se = sc_add(se, acc[q * NB + e]);
+                if (!sc_zero(se)) {
+                    const double f = ldexp(1.0, se.e - S0.e);
+                    const double ax = (double)se.x, ay = (double)se.y, bx = (double)S0.x, by = (double)S0.y;
+                    const double den = bx * bx + by * by;
+                    const double Rx = (ax * bx + ay * by) / den * f, Ry = (ay * bx - ax * by) / den * f;
+                    const double c1 = 0.5 * (double)bondJ(md, aa[e] & 0x7fff);
+                    hx += c1 * Rx;
+                    hy += c1 * Ry;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                hx += __shfl_xor_sync(0xffffffffu, hx, o);
+                hy += __shfl_xor_sync(0xffffffffu, hy, o);
+            }
+            if (lane == 0) {
+                const double h1x = (double)diag_sh + hx;
+                if (!sc_finite(S0) || sc_zero(S0) || !isfinite(h1x) || !isfinite(hy)) flag_range(md.status);
+                h1_out[2 * smp] = h1x;
+                h1_out[2 * smp + 1] = hy;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Paired tables from the connection tables of the model: tp[(r 2 + o) NB + b][k]
+// = (Tx_2k, Tx_2k+1, Ty_2k, Ty_2k+1) for unit pairs k < MH (T = 0 past M), and
+// ep = e^{(1 - 2 o) C_b} as scaled numbers.
+__global__ void k_tables_paired(DevModel<float> md, int MH, float4 *__restrict__ tp, sc<float> *__restrict__ ep)
+{
+    const int NB = md.nbonds;
+    const int64_t tot = (int64_t)md.K * 2 * NB * MH;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rowi = q / MH;
+        const int k = (int)(q - rowi * MH);
+        const cx<float> *src = md.Tb + rowi * md.Mp;
+        const int m0 = 2 * k, m1 = 2 * k + 1;
+        const cx<float> a = m0 < md.M ? src[m0] : cx<float>{0.f, 0.f};
+        const cx<float> b = m1 < md.M ? src[m1] : cx<float>{0.f, 0.f};
+        tp[q] = make_float4(a.x, b.x, a.y, b.y);
+    }
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)md.K * 2 * NB;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int rb = (int)(q / NB);            // r * 2 + o
+        const int b = (int)(q - (int64_t)rb * NB);
+        const int r = rb >> 1, o = rb & 1;
+        const cx<float> c = md.Cb[(size_t)r * NB + b];
+        ep[q] = sc_norm(sc_exp(o ? cx<float>{-c.x, -c.y} : c));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int ef_np(int M) { return (M + 2 * kEfGL - 1) / (2 * kEfGL); }   // unit pairs per lane
+
+static size_t ef_smem(const DevModel<float> &md, int warps)
+{
+    const int MH = kEfGL * ef_np(md.M);
+    return (size_t)md.K * 2 * md.nbonds * MH * sizeof(float4) + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) +
+           (size_t)warps * md.nbonds * sizeof(sc<float>);
+}
+
+static int ef_warps(const DevModel<float> &md)
+{
+    // the most warps (latency hiding) whose row groups idle at most 1/8 of the
+    // time, else the count in 8..16 that idles least
+    const int rows = md.K * md.G;
+    int best = 16, waste = 1 << 30;
+    for (int w = 16; w >= 8; --w) {
+        const int slots = 4 * w;
+        const int pad = (rows + slots - 1) / slots * slots;
+        if (8 * (pad - rows) <= pad) return w;
+        if (pad - rows < waste) { waste = pad - rows; best = w; }
+    }
+    return best;
+}
+
+bool eloc_fast_supported(const DevModel<float> &md)
+{
+    const int np = ef_np(md.M);
+    if (np < 1 || np > 8) return false;
+    return ef_smem(md, ef_warps(md)) <= 222 * 1024;   // with the static shared memory, within 227 KB
+}
+
+size_t eloc_fast_table_bytes(const DevModel<float> &md)
+{
+    const int MH = kEfGL * ef_np(md.M);
+    return (size_t)md.K * 2 * md.nbonds * MH * sizeof(float4) + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) + 256;
+}
+
+cudaError_t launch_tables_paired(const DevModel<float> &md, void *tables, cudaStream_t st)
+{
+    const int MH = kEfGL * ef_np(md.M);
+    float4 *tp = reinterpret_cast<float4 *>(tables);
+    sc<float> *ep = reinterpret_cast<sc<float> *>(tp + (size_t)md.K * 2 * md.nbonds * MH);
+    k_tables_paired<<<256, 256, 0, st>>>(md, MH, tp, ep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eloc_fast(const DevModel<float> &md, const void *tables, const uint64_t *cfg, int64_t n,
+                             double *h1, int nsm, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    EfArgs ea;
+    const int np = ef_np(md.M);
+    ea.MH = kEfGL * np;
+    ea.tp = reinterpret_cast<const float4 *>(tables);
+    ea.ep = reinterpret_cast<const sc<float> *>(ea.tp + (size_t)md.K * 2 * md.nbonds * ea.MH);
+    ea.warps = ef_warps(md);
+    const size_t smem = ef_smem(md, ea.warps);
+    const int grid = (int)(n < nsm ? n : nsm);
+    void (*kern)(DevModel<float>, EfArgs, const uint64_t *, int64_t, double *) = nullptr;
+    switch (np) {
+    case 1: kern = k_eloc_fast<1>; break;
+    case 2: kern = k_eloc_fast<2>; break;
+    case 3: kern = k_eloc_fast<3>; break;
+    case 4: kern = k_eloc_fast<4>; break;
+    case 5: kern = k_eloc_fast<5>; break;
+    case 6: kern = k_eloc_fast<6>; break;
+    case 7: kern = k_eloc_fast<7>; break;
+    default: kern = k_eloc_fast<8>; break;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 32 * ea.warps, smem, st>>>(md, ea, cfg, n, h1);
+    return cudaGetLastError();
+}
+
+}  // namespace nnqs

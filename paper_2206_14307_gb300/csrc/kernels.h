@@ -94,6 +94,16 @@ template <typename T>
 cudaError_t launch_mark_vanishing(const DevModel<T> &md, const uint64_t *cfg, int64_t n, int mode, double *o1,
                                   double *o2, cudaStream_t st);
 
+// FP32 E_loc with the per-bond tables in shared memory (one CTA per SM) and
+// packed FP32x2 arithmetic; supported when a model's tables fit one SM.
+// tables: device buffer of eloc_fast_table_bytes, filled by launch_tables_paired
+// from the model's connection tables.
+bool eloc_fast_supported(const DevModel<float> &md);
+size_t eloc_fast_table_bytes(const DevModel<float> &md);
+cudaError_t launch_tables_paired(const DevModel<float> &md, void *tables, cudaStream_t st);
+cudaError_t launch_eloc_fast(const DevModel<float> &md, const void *tables, const uint64_t *cfg, int64_t n,
+                             double *h1, int nsm, cudaStream_t st);
+
 // checked mode: first_bad <- lowest index of a configuration outside Sz = 0
 // (UINT64_MAX if none)
 cudaError_t launch_check_sz0(const uint64_t *cfg, int64_t n, int nwords, int N, unsigned long long *first_bad,
