@@ -310,6 +310,8 @@ def gpu_arm(args, rank, world):
         res["tc10"] = tc10_leg(flush, min(args.steps, 5))
     if not args.no_mixed:
         res["mixed"] = mixed_leg(flush)
+    if not args.no_sr:
+        res["sr"] = sr_leg(flush, max(1, args.sr_steps))
     return res
 
 
@@ -400,6 +402,60 @@ def tc10_leg(flush, steps):
         m.status()
         m.close()
     return res
+
+
+def sr_leg(flush, steps):
+    """One stochastic-reconfiguration step of the 10x10 configuration (K = 4
+    complex RBMs, alpha = 4 (M = 400), translations x C4v (800 ops), 8192
+    samples; Sec. 3.2 Eq. 12 and Sec. 3.4): sampling (1024 chains x 8, n_skip
+    10, n_burn 100), fresh log psi on the tensor cores, E_loc, the
+    log-derivatives O_k (P = 162004 complex parameters per sample), the
+    energy gradient F and the conjugate-gradient solve of (S + lambda) delta =
+    -dtau F on the device (lambda = 1e-6, at most 50 iterations)."""
+    import torch
+    from paper_2206_14307_gb300 import nnqs, synth
+    L10, N10, M10, K10, NS = 10, 100, 400, 4, 8192
+    p = synth.random_params(N10, M10, K10, std=PARAM_STD, seed=PARAM_SEED, logc_std=0.2)
+    m = nnqs.Model(L10, J1, J2, K=K10, M=M10, proj_t=True, proj_p=True, spin_inv=0, use_bias=True,
+                   precision=nnqs.BF16X2)
+    m.set_params(p)
+    P = m.P
+    cfg = torch.empty(NS, 2, dtype=torch.int64, device="cuda")
+    acc = torch.empty(1024, dtype=torch.float32, device="cuda")
+    lp = torch.empty(NS, 2, dtype=torch.float64, device="cuda")
+    el = torch.empty(NS, 2, dtype=torch.float64, device="cuda")
+    O = torch.empty(NS, P, 2, dtype=torch.float64, device="cuda")
+    F = torch.empty(P, 2, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    times, iters = [], []
+    for k in range(steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        ev[0].record(st)
+        m.sample(rank_seed(0, 900 + k), 1024, 8, N_SKIP, N_BURN, cfg_out=cfg, acc_out=acc)
+        ev[1].record(st)
+        m.log_psi(cfg, out=lp)
+        ev[2].record(st)
+        m.local_energy(cfg, out=el)
+        ev[3].record(st)
+        m.grad_logpsi(cfg, out=O)
+        ev[4].record(st)
+        m.energy_grad(O, el, out=F)
+        ev[5].record(st)
+        delta, info = m.sr_solve(O, F, lam=1e-6, dtau=0.01, max_iter=50, tol=1e-6)
+        ev[6].record(st)
+        ev[6].synchronize()
+        if k > 0:   # the first step is the warm-up
+            times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(6)])
+            iters.append(float(info[0].item()))
+    m.status()
+    t = np.mean(np.array(times), axis=0)
+    m.close()
+    del O
+    return dict(ms=float(t.sum()), stages=dict(sample=t[0], log_psi=t[1], local_energy=t[2], grad_logpsi=t[3],
+                                                energy_grad=t[4], sr_solve=t[5]),
+                samples=NS, P=P, cg_iterations=float(np.mean(iters)), steps=steps)
 
 
 def mixed_leg(flush):
@@ -505,6 +561,44 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(name):
+    """One small launch of one kernel of the hot path (after two warm-up calls),
+    for profiler captures; prints the launch's own event time, no bench line.
+      tc10    tensor-core log psi, 10x10 K=4 M=400, 2048 random Sz=0 configurations
+      tc6     tensor-core log psi, the 6x6 model, 4096 configurations
+      eloc6   E_loc, the 6x6 model, 2048 configurations
+      sample6 the sampler, the 6x6 model, 76 chains x 4 samples (n_skip 10, n_burn 40)"""
+    import torch
+    from paper_2206_14307_gb300 import nnqs, synth
+    if name == "tc10":
+        Lc, Mc, Kc, inv, n = 10, 400, 4, 0, 2048
+    else:
+        Lc, Mc, Kc, inv, n = L, M, 1, 1, 4096 if name == "tc6" else 2048
+    Nc = Lc * Lc
+    p = synth.random_params(Nc, Mc, Kc, std=PARAM_STD, seed=PARAM_SEED, logc_std=0.2 if Kc > 1 else None)
+    m = nnqs.Model(Lc, J1, J2, K=Kc, M=Mc, proj_t=True, proj_p=True, spin_inv=inv, use_bias=True,
+                   precision=nnqs.BF16X2)
+    m.set_params(p)
+    cfg = nnqs.cfg_tensor(synth.pack(synth.random_sz0(Nc, n, seed=21)))
+    out = torch.empty(n, 2, dtype=torch.float64, device="cuda")
+    if name.startswith("tc"):
+        run = lambda: m.log_psi(cfg, out=out)
+    elif name == "eloc6":
+        run = lambda: m.local_energy(cfg, out=out)
+    else:
+        run = lambda: m.sample(14307, 76, 4, N_SKIP, 40)
+    run()
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run()
+    e1.record()
+    e1.synchronize()
+    m.status()
+    print(f"case {name}: {e0.elapsed_time(e1):.3f} ms", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -518,9 +612,18 @@ def main():
     ap.add_argument("--lanczos-steps", type=int, default=2)
     ap.add_argument("--no-tc10", action="store_true", help="skip the 10x10 fresh-amplitude leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 64-instance mixed batch")
+    ap.add_argument("--no-sr", action="store_true", help="skip the 10x10 SR step")
+    ap.add_argument("--sr-steps", type=int, default=1)
     ap.add_argument("--small", action="store_true",
                     help="128 chains and a 512-sample Lanczos leg (for profiler captures; not a bench line)")
+    ap.add_argument("--case", choices=["tc10", "tc6", "eloc6", "sample6"],
+                    help="one small launch of one kernel for profiler captures (no bench line)")
     args = ap.parse_args()
+    if args.case:
+        from paper_2206_14307_gb300 import build as B
+        B.build()
+        profile_case(args.case)
+        return
     if args.small:
         global N_CHAINS, N_SAMPLES, LZ_SAMPLES, LZ_SUBSET
         N_CHAINS = 128
@@ -646,6 +749,22 @@ def main():
                                            "alpha in {1,2,4}, K in {1,2}, 8N ops; 256 samples each",
                                "value": mx["samples"] / (mx["ms"] / 1e3), "unit": "Lanczos samples/s",
                                "ms_per_step": mx["ms"], "autotune_s": mx["autotune_s"], "shapes": mx["shapes"]}
+    if "sr" in res:
+        sr = res["sr"]
+        stg = sr["stages"]
+        # CG: every iteration reads O twice (O x and O^H z): 2 n P complex doubles
+        cg_bytes = 2.0 * sr["samples"] * sr["P"] * 16 * max(1.0, sr["cg_iterations"])
+        cg_gbs = cg_bytes / (stg["sr_solve"] / 1e3) / 1e9
+        line["sr_step_10x10"] = {
+            "workload": "10x10 J1-J2, K=4 complex RBMs alpha=4 (M=400), 800 ops; 8192 samples; sample + log psi + "
+                        "E_loc + O_k (P=162004) + F + CG (lambda 1e-6, <= 50 iterations)",
+            "value": sr["samples"] / (sr["ms"] / 1e3), "unit": "SR-step samples/s", "ms_per_step": sr["ms"],
+            "steps": sr["steps"], "warmup": 1, "stages_ms": {k: float(v) for k, v in stg.items()},
+            "cg_iterations": sr["cg_iterations"],
+            "cg_roofline": {"kernel": "k_ov + k_sr_out (S x products of the CG)", "bound": "hbm",
+                            "achieved": cg_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": cg_gbs / HBM_PEAK_GBS,
+                            "peak_source": f"HBM copy bandwidth ({PEAK_SOURCE})",
+                            "work": "2 n P x 16 B of O per CG iteration"}}
     if not args.no_cpu:
         if "lanczos" in line:
             line["lanczos"]["cpu_baseline"] = cpu_baseline_lanczos()

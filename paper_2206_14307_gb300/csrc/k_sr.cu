@@ -14,6 +14,7 @@ namespace nnqs {
 
 constexpr int kSrThreads = 256;
 constexpr int kDotBlocks = 128;
+constexpr int kSrChunksMax = 128;   // sample chunks of the two-pass S x product
 
 // scratch layout (doubles)
 //   [0, 16)          CG state: 0 rr, 1 pAp, 2 alpha, 3 beta, 4 |b|^2, 5 done, 6 iterations, 7 W, 8-9 mean
@@ -24,7 +25,9 @@ constexpr int kStateDoubles = 16;
 
 size_t sr_scratch_doubles(int64_t n, int64_t P)
 {
-    return kStateDoubles + 2 * kDotBlocks + 2 * (size_t)n + 6 * (size_t)P + 64;
+    // state, dot partials, z [n][2], r, p, Ap [P][2], the matvec's state block,
+    // and the chunk partials [kSrChunks][P][4] of the S x product
+    return kStateDoubles + 2 * kDotBlocks + 2 * (size_t)n + 6 * (size_t)P + 64 + (size_t)kSrChunksMax * 4 * (size_t)P;
 }
 
 template <int NV>
@@ -112,23 +115,45 @@ __global__ void __launch_bounds__(kSrThreads) k_ov(const double *__restrict__ O,
     if (threadIdx.x == 0) { z[2 * s] = a[0]; z[2 * s + 1] = a[1]; }
 }
 
-// y_k = (1/W) sum_s w_s conj(O_sk) z_s - conj(Obar_k) zbar + lambda x_k
-__global__ void k_sr_out(const double *__restrict__ O, const double *__restrict__ z, const double *__restrict__ w,
-                         const double *__restrict__ zst, const double *__restrict__ x, double lambda, int64_t n,
-                         int64_t P, double *__restrict__ y, const double *__restrict__ state)
+// y_k = (1/W) sum_s w_s conj(O_sk) z_s - conj(Obar_k) zbar + lambda x_k, in two
+// passes over sample chunks: pass 1 (block (k tile, chunk c)) sums samples of
+// chunk c for 256 consecutive k -- coalesced rows of O -- into part[c][k];
+// pass 2 adds the chunks in order (deterministic) and forms y.
+constexpr int kSrChunks = kSrChunksMax;
+__global__ void __launch_bounds__(256) k_sr_part(const double *__restrict__ O, const double *__restrict__ z,
+                                                 const double *__restrict__ w, int64_t n, int64_t P, int64_t chunk,
+                                                 double *__restrict__ part, const double *__restrict__ state)
+{
+    if (state && state[S_DONE] != 0.0) return;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const int64_t s0 = blockIdx.y * chunk, s1 = s0 + chunk < n ? s0 + chunk : n;
+    double ax = 0, ay = 0, mx = 0, my = 0;
+#pragma unroll 4
+    for (int64_t s = s0; s < s1; ++s) {
+        const double ws = w ? w[s] : 1.0;
+        const double2 o = *reinterpret_cast<const double2 *>(O + (s * P + k) * 2);
+        const double zx = z[2 * s], zy = z[2 * s + 1];
+        ax += ws * (o.x * zx + o.y * zy);
+        ay += ws * (o.x * zy - o.y * zx);
+        mx += ws * o.x;
+        my += ws * o.y;
+    }
+    double *pp = part + ((int64_t)blockIdx.y * P + k) * 4;
+    pp[0] = ax; pp[1] = ay; pp[2] = mx; pp[3] = my;
+}
+
+__global__ void k_sr_out(const double *__restrict__ part, int nch, const double *__restrict__ zst,
+                         const double *__restrict__ x, double lambda, int64_t P, double *__restrict__ y,
+                         const double *__restrict__ state)
 {
     if (state && state[S_DONE] != 0.0) return;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= P) return;
     double ax = 0, ay = 0, mx = 0, my = 0;
-    for (int64_t s = 0; s < n; ++s) {
-        const double ws = w ? w[s] : 1.0;
-        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
-        const double zx = z[2 * s], zy = z[2 * s + 1];
-        ax += ws * (ox * zx + oy * zy);
-        ay += ws * (ox * zy - oy * zx);
-        mx += ws * ox;
-        my += ws * oy;
+    for (int c = 0; c < nch; ++c) {
+        const double *pp = part + ((int64_t)c * P + k) * 4;
+        ax += pp[0]; ay += pp[1]; mx += pp[2]; my += pp[3];
     }
     const double inv = 1.0 / zst[S_W];
     ax *= inv; ay *= inv; mx *= inv; my *= inv;
@@ -138,11 +163,14 @@ __global__ void k_sr_out(const double *__restrict__ O, const double *__restrict_
 }
 
 static void matvec(const double *O, const double *w, int64_t n, int64_t P, const double *x, double lambda, double *y,
-                   double *z, double *zst, const double *state, cudaStream_t st)
+                   double *z, double *zst, double *part, const double *state, cudaStream_t st)
 {
+    const int64_t chunk = (n + kSrChunks - 1) / kSrChunks;
+    const int nch = (int)((n + chunk - 1) / chunk);
     k_ov<<<(unsigned)n, kSrThreads, 0, st>>>(O, x, P, z, state);
     k_wmean<<<1, kSrThreads, 0, st>>>(z, w, n, zst);
-    k_sr_out<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(O, z, w, zst, x, lambda, n, P, y, state);
+    k_sr_part<<<dim3((unsigned)((P + 255) / 256), (unsigned)nch), 256, 0, st>>>(O, z, w, n, P, chunk, part, state);
+    k_sr_out<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(part, nch, zst, x, lambda, P, y, state);
 }
 
 cudaError_t launch_sr_matvec(const double *O, const double *w, int64_t n, int64_t P, const double *x, double lambda,
@@ -150,7 +178,8 @@ cudaError_t launch_sr_matvec(const double *O, const double *w, int64_t n, int64_
 {
     double *zst = scratch;                                     // its own small state block
     double *z = scratch + kStateDoubles + 2 * kDotBlocks;
-    matvec(O, w, n, P, x, lambda, y, z, zst, nullptr, st);
+    double *part = z + 2 * n + 6 * P + 64;
+    matvec(O, w, n, P, x, lambda, y, z, zst, part, nullptr, st);
     return cudaGetLastError();
 }
 
@@ -239,12 +268,13 @@ cudaError_t launch_sr_solve(const double *O, const double *w, int64_t n, int64_t
     double *z = part + 2 * kDotBlocks;
     double *r = z + 2 * n, *p = r + 2 * P, *Ap = p + 2 * P;
     double *zst = Ap + 2 * P;   // state block of the matvec means (16 doubles)
+    double *cpart = zst + 64;   // chunk partials of the S x product
     const unsigned gp = (unsigned)((P + 255) / 256);
     k_cg_init<<<gp, 256, 0, st>>>(F, dtau, P, x, r, p);
     k_dot_partial<<<kDotBlocks, kSrThreads, 0, st>>>(r, r, P, part);
     k_dot_final<<<1, 32, 0, st>>>(part, kDotBlocks, state, 0, tol);
     for (int it = 0; it < max_iter; ++it) {
-        matvec(O, w, n, P, p, lambda, Ap, z, zst, state, st);
+        matvec(O, w, n, P, p, lambda, Ap, z, zst, cpart, state, st);
         k_dot_partial<<<kDotBlocks, kSrThreads, 0, st>>>(p, Ap, P, part);
         k_dot_final<<<1, 32, 0, st>>>(part, kDotBlocks, state, 1, tol);
         k_cg_update<<<gp, 256, 0, st>>>(P, x, r, p, Ap, state);
