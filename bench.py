@@ -99,13 +99,14 @@ MUFU_EX2_GOPS = float(ALU_PEAKS["mufu_ex2_gops"])
 # the running product prod *= f (a complex multiply), i.e. 8 FMA-pipe issue
 # slots = 16 peak-equivalent flop.
 FLOPS_PER_ELEMENT = 16
-# DRAM bytes (read + write) per launch, from the ncu captures of the current
-# kernels on the 2048-sample (E_loc) and 512-sample (Lanczos) cases; the
-# traffic grows with the samples, so the full launches move 8x that.
-K_RATIO_TRAFFIC = 8 * 0.217856e6
-K_LANCZOS_TRAFFIC = 8 * 1.236224e6
-# k_sample: 9.214 GB written + 14.9 MB read per 128-chain launch, x8 for 1024 chains
-K_SAMPLE_TRAFFIC = 8 * (9.214206e9 + 14.924544e6)
+# DRAM bytes (read + write) of one full launch of the kernel a roofline names,
+# from ncu captures of the current kernel (None: not captured since it last
+# changed).
+K_RATIO_TRAFFIC = None
+K_LANCZOS_TRAFFIC = None
+# Shared-memory bandwidth of the SMs, 128 B per clock per SM at the maximum SM
+# clock (derived, not measured): the roof of the sampler's cache stream.
+SMEM_PEAK_GBS = 128 * 152 * 2.07
 
 
 LZ_L, LZ_M, LZ_SAMPLES, LZ_SUBSET = 8, 128, 4096, 912   # subset: 6 x 152 SMs
@@ -567,17 +568,20 @@ def profile_case(name):
       tc10    tensor-core log psi, 10x10 K=4 M=400, 2048 random Sz=0 configurations
       tc6     tensor-core log psi, the 6x6 model, 4096 configurations
       eloc6   E_loc, the 6x6 model, 2048 configurations
-      sample6 the sampler, the 6x6 model, 76 chains x 4 samples (n_skip 10, n_burn 40)"""
+      sample6 the sampler, the 6x6 model, 76 chains x 4 samples (n_skip 10, n_burn 40)
+      lz8     h1 and h2 of the 8x8 Lanczos model (M = 128, |G| = 512), 152 random Sz=0 configurations"""
     import torch
     from paper_2206_14307_gb300 import nnqs, synth
     if name == "tc10":
         Lc, Mc, Kc, inv, n = 10, 400, 4, 0, 2048
+    elif name == "lz8":
+        Lc, Mc, Kc, inv, n = LZ_L, LZ_M, 1, 0, 152
     else:
         Lc, Mc, Kc, inv, n = L, M, 1, 1, 4096 if name == "tc6" else 2048
     Nc = Lc * Lc
     p = synth.random_params(Nc, Mc, Kc, std=PARAM_STD, seed=PARAM_SEED, logc_std=0.2 if Kc > 1 else None)
     m = nnqs.Model(Lc, J1, J2, K=Kc, M=Mc, proj_t=True, proj_p=True, spin_inv=inv, use_bias=True,
-                   precision=nnqs.BF16X2)
+                   precision=nnqs.FP32 if name == "lz8" else nnqs.BF16X2)
     m.set_params(p)
     cfg = nnqs.cfg_tensor(synth.pack(synth.random_sz0(Nc, n, seed=21)))
     out = torch.empty(n, 2, dtype=torch.float64, device="cuda")
@@ -585,6 +589,8 @@ def profile_case(name):
         run = lambda: m.log_psi(cfg, out=out)
     elif name == "eloc6":
         run = lambda: m.local_energy(cfg, out=out)
+    elif name == "lz8":
+        run = lambda: m.lanczos(cfg)
     else:
         run = lambda: m.sample(14307, 76, 4, N_SKIP, 40)
     run()
@@ -616,7 +622,7 @@ def main():
     ap.add_argument("--sr-steps", type=int, default=1)
     ap.add_argument("--small", action="store_true",
                     help="128 chains and a 512-sample Lanczos leg (for profiler captures; not a bench line)")
-    ap.add_argument("--case", choices=["tc10", "tc6", "eloc6", "sample6"],
+    ap.add_argument("--case", choices=["tc10", "tc6", "eloc6", "sample6", "lz8"],
                     help="one small launch of one kernel for profiler captures (no bench line)")
     args = ap.parse_args()
     if args.case:
@@ -687,18 +693,17 @@ def main():
                        "fresh_amplitudes_per_s": N_SAMPLES / (res["ms_logpsi"] / 1e3),
                        "note": "algorithmic flop (4 K|G| M N per amplitude); the bf16 hi+lo split executes 2x; "
                                "the kernel is limited by its log-cosh epilogue, not the MMA"},
-        "sampler": {"kernel": "k_sample (Metropolis proposals with the speculative p-cache update)",
-                    "bound": "issue",
-                    "bound_note": "dependent arithmetic and per-step CTA barriers (ncu: issue-active, wait, "
-                                  "long_scoreboard and barrier stalls); the cache stream stays in L2 and DRAM "
-                                  "runs far below its peak, so the kernel is not HBM-bound",
-                    "achieved": samp_bytes / samp_s / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                    "frac": samp_bytes / samp_s / 1e9 / HBM_PEAK_GBS,
-                    "frac_kind": "algorithmic theta-cache stream (8 K|G|M (1 + acceptance) B per proposal) "
-                                 "against the HBM copy bandwidth",
-                    "dram_gbs": K_SAMPLE_TRAFFIC / samp_s / 1e9,
-                    "dram_frac": K_SAMPLE_TRAFFIC / samp_s / 1e9 / HBM_PEAK_GBS,
-                    "peak_source": f"HBM copy bandwidth ({PEAK_SOURCE})", "traffic": K_SAMPLE_TRAFFIC,
+        "sampler": {"kernel": "k_sample_cl (cluster sampler, each chain's cache in distributed shared memory)",
+                    "bound": "latency",
+                    "bound_note": "each Metropolis step of a chain is serial: the ratio pass over the chain's "
+                                  "cache, the exchange of partial sums over distributed shared memory, one "
+                                  "cluster barrier and the decision (ncu: short_scoreboard, wait and barrier "
+                                  "stalls); DRAM carries only the tables and the kept samples",
+                    "achieved": samp_bytes / samp_s / 1e9, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
+                    "frac": samp_bytes / samp_s / 1e9 / SMEM_PEAK_GBS,
+                    "frac_kind": "algorithmic cache stream (8 K|G|M (1 + acceptance) B per proposal) read from "
+                                 "shared memory, against 128 B/clock/SM at 2.07 GHz (derived)",
+                    "traffic": None,
                     "work": f"{proposals} proposals x {samp_per:.0f} B", "ms": res["ms_sample"]},
         "e2e": {"value": world * res["evals"] / (e2e_ms / 1e3), "unit": "amplitude evals/s",
                 "h2d_bytes_per_step": 2665 * 16, "d2h_bytes_per_step": 32},
@@ -721,7 +726,7 @@ def main():
             "steps": args.lanczos_steps, "warmup": 1, "dtype": "f32 (FP64 moments)",
             "E_p1_per_site": lz["e_p1"], "m1_per_site": lz["m1"],
             "flip_sets_per_sample": lz["entries"] / lz["samples"],
-            "roofline": {"kernel": "k_eloc Lanczos mode (all flip-set kinds)", "bound": "alu",
+            "roofline": {"kernel": "k_lanczos_fast (h1, h2 with the per-site tables in shared memory)", "bound": "alu",
                          "achieved": lz_ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": lz_ach / FP32_PEAK_TFLOPS, "traffic": K_LANCZOS_TRAFFIC,
                          "work": f"{lz['entries']} flip sets x |G|={lz['G']} x M={Ml} x {FLOPS_PER_ELEMENT} flop"},

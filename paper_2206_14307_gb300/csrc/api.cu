@@ -132,6 +132,7 @@ struct nnqs_model {
     int *status = nullptr;
     unsigned long long *chk = nullptr;  // checked mode: first configuration outside Sz = 0
     void *eft = nullptr;                // FP32 E_loc: paired per-bond tables (nullptr: not supported)
+    void *lft = nullptr;                // FP32 h1/h2: paired per-site factors (nullptr: not supported)
     void *ws = nullptr;
     size_t ws_bytes = 0;
 };
@@ -221,6 +222,10 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 cudaError_t mark_vanishing(const nnqs_model *m, const uint64_t *cfg, int64_t n, int mode, double *o1, double *o2,
                            cudaStream_t st);
 
+// h1 and h2 of n configurations on the model's engine: the shared-memory
+// site-table form where it applies (FP32), else the general one.
+cudaError_t lanczos_h(const nnqs_model *m, const uint64_t *cfg, int64_t n, double *h1, double *h2, cudaStream_t st);
+
 // Checked mode (desc.check_inputs): rejects a batch of configurations with
 // NNQS_EINVAL if any lies outside the Sz = 0 sector or sets bits past site
 // N - 1.  Runs one small kernel and synchronises the stream; a no-op when the
@@ -241,6 +246,13 @@ int check_cfg(const nnqs_model *m, const uint64_t *cfg, int64_t n, cudaStream_t 
     for (int k = 0; k < m->nwords; ++k) up += __builtin_popcountll(w[k]);
     return fail(NNQS_EINVAL, "configuration %llu is not a valid Sz = 0 state of %d sites (%d bits set)", bad, m->N,
                 up);
+}
+
+cudaError_t lanczos_h(const nnqs_model *m, const uint64_t *cfg, int64_t n, double *h1, double *h2, cudaStream_t st)
+{
+    if (m->fp64) return launch_ratio(view<double>(m), cfg, n, 1, h1, h2, m->nsm, st);
+    if (m->lft && !test_old_engine()) return launch_lanczos_fast(view<float>(m), m->lft, cfg, n, h1, h2, m->nsm, st);
+    return launch_ratio(view<float>(m), cfg, n, 1, h1, h2, m->nsm, st);
 }
 
 cudaError_t mark_vanishing(const nnqs_model *m, const uint64_t *cfg, int64_t n, int mode, double *o1, double *o2,
@@ -332,6 +344,7 @@ static int create_model(const nnqs_desc *desc, int mp_min, nnqs_model **out)
         DevModel<float> v{};
         v.K = d.K; v.M = d.M; v.N = m->N; v.G = m->G; v.nbonds = (int)bi.size(); v.Mp = m->Mp;
         if (eloc_fast_supported(v)) ALLOC(m->eft, eloc_fast_table_bytes(v));
+        if (lanczos_fast_supported(v)) ALLOC(m->lft, lanczos_fast_table_bytes(v));
     }
     if (d.precision == NNQS_BF16X2 || d.precision == NNQS_BF16X3) {
         const int ns = d.precision == NNQS_BF16X2 ? 2 : 3;
@@ -390,7 +403,7 @@ int nnqs_destroy(nnqs_model *m)
     if (!m) return NNQS_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {m->perm, m->bi, m->bj, m->bt, m->chi, m->params, m->Wt, m->b, m->a, m->logc, m->X, m->XA,
-                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->chk, m->eft, m->ws, m->bimg, m->pinv};
+                    m->Tb, m->Cb, m->S4, m->CS, m->ES, m->bperm, m->status, m->chk, m->eft, m->lft, m->ws, m->bimg, m->pinv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -431,6 +444,10 @@ int nnqs_set_params_device(nnqs_model *m, const double *params, int64_t P, void 
         if (m->eft) {
             e = launch_tables_paired(view<float>(m), m->eft, st);
             if (e != cudaSuccess) return cuda_fail(e, "build paired tables");
+        }
+        if (m->lft) {
+            e = launch_tables_site_paired(view<float>(m), m->lft, st);
+            if (e != cudaSuccess) return cuda_fail(e, "build paired site tables");
         }
         if (m->ns) {
             e = launch_bimg(m->params, m->N, m->d.M, m->G, m->d.K, m->nsign, m->ns, m->d.use_bias, m->bimg, st);
@@ -518,8 +535,7 @@ int nnqs_lanczos_moments(nnqs_model *m, const uint64_t *cfg, int64_t n, double *
         char *ws = (char *)m->ws;
         double *H1 = h1 ? h1 : (double *)(ws + off_h1);
         double *H2 = h2 ? h2 : (double *)(ws + off_h2);
-        cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, H1, H2, m->nsm, st)
-                                : launch_ratio(view<float>(m), cfg, n, 1, H1, H2, m->nsm, st);
+        cudaError_t e = lanczos_h(m, cfg, n, H1, H2, st);
         if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 1, H1, H2, st);
         if (e != cudaSuccess) return cuda_fail(e, "lanczos");
         if (moments || lanczos) {
@@ -555,8 +571,7 @@ int nnqs_lanczos_partial(nnqs_model *m, const uint64_t *cfg, int64_t n, double *
         char *ws = (char *)m->ws;
         double *H1 = h1 ? h1 : (double *)(ws + off_h1);
         double *H2 = h2 ? h2 : (double *)(ws + off_h2);
-        cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, H1, H2, m->nsm, st)
-                                : launch_ratio(view<float>(m), cfg, n, 1, H1, H2, m->nsm, st);
+        cudaError_t e = lanczos_h(m, cfg, n, H1, H2, st);
         if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 1, H1, H2, st);
         if (e == cudaSuccess) e = launch_moments(H1, H2, n, (double *)ws, nb, nullptr, nullptr, st, sums);
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "lanczos_partial");
@@ -731,8 +746,7 @@ int nnqs_lanczos_moments_noalloc(nnqs_model *m, const uint64_t *cfg, int64_t n, 
         double *partial = base + 4 * (size_t)NNQS_NOALLOC_MAX_SAMPLES;
         cudaStream_t st = (cudaStream_t)stream;
         if (int rc = check_cfg(m, cfg, n, st)) return rc;
-        cudaError_t e = m->fp64 ? launch_ratio(view<double>(m), cfg, n, 1, h1, h2, m->nsm, st)
-                                : launch_ratio(view<float>(m), cfg, n, 1, h1, h2, m->nsm, st);
+        cudaError_t e = lanczos_h(m, cfg, n, h1, h2, st);
         if (e == cudaSuccess) e = mark_vanishing(m, cfg, n, 1, h1, h2, st);
         if (e != cudaSuccess) return cuda_fail(e, "lanczos (fixed scratch)");
         if (moments || lanczos) {
@@ -789,8 +803,7 @@ int nnqs_lanczos2(nnqs_model *m, const uint64_t *cfg, int64_t n, double *h3_out,
         };
         auto ratio = [&](const uint64_t *c, int64_t k, double *a, double *b) -> cudaError_t {
             if (k == 0) return cudaSuccess;
-            const cudaError_t e2 = m->fp64 ? launch_ratio(view<double>(m), c, k, 1, a, b, m->nsm, st)
-                                           : launch_ratio(view<float>(m), c, k, 1, a, b, m->nsm, st);
+            const cudaError_t e2 = lanczos_h(m, c, k, a, b, st);
             return e2 == cudaSuccess ? mark_vanishing(m, c, k, 1, a, b, st) : e2;
         };
         e = m->fp64 ? launch_fill_nb(view<double>(m), cfg, n, off, ncfg, ncoef, st)

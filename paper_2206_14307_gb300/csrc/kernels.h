@@ -104,6 +104,18 @@ cudaError_t launch_tables_paired(const DevModel<float> &md, void *tables, cudaSt
 cudaError_t launch_eloc_fast(const DevModel<float> &md, const void *tables, const uint64_t *cfg, int64_t n,
                              double *h1, int nsm, cudaStream_t st);
 
+// FP32 h1 and h2 (the Lanczos quantities) with the per-site factor tables in
+// shared memory (one CTA per SM): second-level flip sets as exchanges in the
+// once-exchanged configuration.  Supported when a model's site tables fit one
+// SM next to the flip-set lists; tables: device buffer of
+// lanczos_fast_table_bytes, filled by launch_tables_site_paired from the
+// model's per-site tables.
+bool lanczos_fast_supported(const DevModel<float> &md);
+size_t lanczos_fast_table_bytes(const DevModel<float> &md);
+cudaError_t launch_tables_site_paired(const DevModel<float> &md, void *tables, cudaStream_t st);
+cudaError_t launch_lanczos_fast(const DevModel<float> &md, const void *tables, const uint64_t *cfg, int64_t n,
+                                double *h1, double *h2, int nsm, cudaStream_t st);
+
 // checked mode: first_bad <- lowest index of a configuration outside Sz = 0
 // (UINT64_MAX if none)
 cudaError_t launch_check_sz0(const uint64_t *cfg, int64_t n, int nwords, int N, unsigned long long *first_bad,
