@@ -129,6 +129,45 @@ template <typename T> __device__ __forceinline__ cx<T> warp_sum(cx<T> v)
     return v;
 }
 
+// product of a scaled number and a double complex, as a scaled double
+__device__ __forceinline__ sc<double> sd_mul(sc<float> a, double bx, double by)
+{
+    const double x = (double)a.x * bx - (double)a.y * by, y = (double)a.x * by + (double)a.y * bx;
+    return sc_norm(sc<double>{x, y, a.e});
+}
+
+// a scaled number as a double complex
+__device__ __forceinline__ void sc_to_d(sc<float> a, double &x, double &y)
+{
+    const double f = pow2i<double>(a.e);
+    x = (double)a.x * f;
+    y = (double)a.y * f;
+}
+
+// product over the GL lanes of an aligned lane group (every lane receives it)
+template <int GL> __device__ __forceinline__ sc<float> group_prod(sc<float> v)
+{
+    v = sc_norm(v);
+#pragma unroll
+    for (int o = GL / 2; o > 0; o >>= 1) {
+        const sc<float> w{shfl_x(v.x, o), shfl_x(v.y, o), __shfl_xor_sync(0xffffffffu, v.e, o)};
+        v = sc_mul(v, w);
+    }
+    return v;
+}
+
+// (x, y) <- mantissa of max(|x|, |y|) in [1, 2); returns the binary exponent.
+// Exponent bits only: zero stays zero (exponent -127), a non-finite input
+// stays non-finite.
+__device__ __forceinline__ int nrm(float &x, float &y)
+{
+    const uint32_t bits = __float_as_uint(fmaxf(fabsf(x), fabsf(y))) & 0x7f800000u;
+    const float s = __uint_as_float(0x7f000000u - bits);
+    x *= s;
+    y *= s;
+    return (int)(bits >> 23) - 127;
+}
+
 // exp(z) as a scaled number (exact exponent split of Re z)
 template <typename T> __device__ __forceinline__ sc<T> sc_exp(cx<T> z)
 {

@@ -3,45 +3,152 @@
 //
 // For a sample s, a row t = (r, g, sign) of the projected sum (Eqs. 4-6) with
 // p_m = e^{theta_m}/(2cosh theta_m), and an anti-aligned bond b, the row's ratio
-// is e^{C} prod_m (1 + p_m T_m): T = e^{2 Delta} - 1 and the prefactor exponent
-// C belong to the bond's image b' = g(b) and its orientation (the tables of the
-// connected-configuration engine).  Then
-//   E_loc = diag(s) + sum_b (J_b/2) [sum_t w_t ratio_{t,b}] / [sum_t w_t],
-// w_t = c_r chi(g) chi_P e^{+-a.T_g s} prod_m 2cosh(theta_m) the row's term.
+// is e^{C} prod_m (1 + p_m (U_m - 1)): U = e^{2 Delta} and the prefactor
+// exponent C belong to the bond's image b' = g(b) and its orientation (the
+// tables of the connected-configuration engine).  With q_m = (1 - p_m)/p_m
+// the factor is p_m (q_m + U_m); the product of the p_m is the row's, so per
+// element the work is q + U (two packed adds) and the running product.  Then
+//   E_loc = diag(s) + [sum_t w_t P_t sum_b (J_b/2) e^{C_b} prod_m (q_m + U_m)]
+//                     / [sum_t w_t],
+// w_t = c_r chi(g) chi_P e^{+-a.T_g s} prod_m 2cosh(theta_m) the row's term and
+// P_t = prod_m p_m.  A row whose group has some |p_m| < 2^-12 (q above 2^12)
+// takes the plain factors 1 + p_m (U_m - 1) instead.
 //
 // Layout: one CTA per SM (the tables of one model, 2 x 4N rows per RBM, are
 // copied into its shared memory once), one sample at a time.  A group of 8
 // lanes owns a row; lane l owns the unit pairs k = l + 8 j (units 2k, 2k + 1),
-// whose p sit in registers as packed pairs.  The table row of a bond image is
-// stored as float4 (Tx_2k, Tx_2k+1, Ty_2k, Ty_2k+1) per pair, so a group reads
-// one contiguous 128-byte row segment per step (conflict-free) and
-// (1 + p T) and the running products of the even and odd units are packed
-// FP32x2 operations.  Entries (anti-aligned bonds) go 8 at a time: lane l
-// decodes entry l (image bond, orientation, prefactor) and the group shares
-// the table offsets by shuffle; a butterfly product-reduce-scatter over the
-// group leaves lane l with entry l's full product, which it weights by the
-// prefactor and the row term and adds into the warp's sum for that entry.
+// whose q sit in registers as packed pairs.  The table row of a bond image is
+// stored as float4 (Ux_2k, Ux_2k+1, Uy_2k, Uy_2k+1) per pair, so a group reads
+// one contiguous 128-byte row segment per step (conflict-free).  Entries
+// (anti-aligned bonds) go 8 at a time: lane l decodes entry l (image bond,
+// orientation, prefactor) and the group shares the table offsets by shuffle; a
+// butterfly product-reduce-scatter over the group leaves lane l with entry l's
+// full product, which it weights and adds into its FP32 sum for the row.
+#include <cstdlib>
+
 #include "common.cuh"
 #include "f2.cuh"
 #include "kernels.h"
 
 namespace nnqs {
 
-constexpr int kEfGL = 8;                 // lanes per row group
+constexpr int kEfGL = 8;             // lanes per row group
 constexpr int kEfMaxThreads = 512;   // at most 16 warps (128 registers per thread)
 
 struct EfArgs {
-    const float4 *tp;     // [K][2][NB][MH] paired per-bond tables T
+    const float4 *tp;     // [K][2][NB][MH] paired per-bond tables U = 1 + T
     const sc<float> *ep;  // [K][2][NB] e^{+C}, e^{-C}
     int MH;               // unit pairs per table row (8 NP)
     int warps;
+    int plain;            // 1: every row takes the plain factors (test hook)
 };
 
-// scaled product of two scaled complex numbers, unnormalised exponents kept exact
-__device__ __forceinline__ void scm(float &x, float &y, int &e, float x2, float y2, int e2)
+// The entries of one row and sign, 8 at a time: sum over the anti-aligned
+// bonds of (J_b/2) e^{C_b} prod_m f_m into the owner lanes' (accx, accy)
+// (FP32, scaled by 2^eref) or, outside the FP32 window, (Ox, Oy).
+// QF: f = q + U (ca, cb = q); else f = 1 + p (U - 1) (ca, cb, cc = Re p,
+// Im p, -Im p).
+template <int NP, bool QF>
+__device__ __forceinline__ void ef_entries(const DevModel<float> &md, const float4 *tps, const sc<float> *eps,
+                                           const uint16_t *aa, const uint16_t *bps, int naa, int r, int sg, int MH,
+                                           const f2 (&ca)[NP], const f2 (&cb)[NP], const f2 (&cc)[NP], int eref,
+                                           int gl, int gbase, float &accx, float &accy, double &Ox, double &Oy)
 {
-    const float nx = x * x2 - y * y2, ny = x * y2 + y * x2;
-    x = nx; y = ny; e += e2;
+    const int NB = md.nbonds;
+    const f2 one2 = f2_pack(1.f, 1.f);
+    for (int e0 = 0; e0 < naa; e0 += kEfGL) {
+        // lane gl: table offset and weighted prefactor of entry e0 + gl
+        const int e = e0 + gl;
+        int off = 0;
+        sc<float> pre{0.f, 0.f, 0};
+        if (e < naa) {
+            const uint16_t code = aa[e];
+            const int b = code & 0x7fff;
+            const uint16_t bp = bps[b];
+            const int bb = bp & 0x7fff;
+            // orientation of the exchange on the image bond, for this sign
+            const bool pos = ((code >> 15) != 0) != ((bp >> 15) != 0);   // s_i flip-corrected
+            const int o = (pos != (sg != 0)) ? 0 : 1;
+            off = ((r * 2 + o) * NB + bb) * MH;
+            pre = eps[(r * 2 + o) * NB + bb];
+            const float c1 = 0.5f * bondJ(md, b);
+            pre.x *= c1;
+            pre.y *= c1;
+        }
+        float rx[kEfGL], ry[kEfGL];
+        int re[kEfGL];
+#pragma unroll
+        for (int q = 0; q < kEfGL; ++q) {
+            const float4 *trow = tps + __shfl_sync(0xffffffffu, off, gbase + q) + gl;
+            // running products of the even and odd units (packed)
+            f2 Rx = one2, Ry = 0;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                f2 ux, uy;
+                lds128(trow + kEfGL * j, ux, uy);
+                f2 fx, fy;
+                if constexpr (QF) {
+                    fx = add2(ux, ca[j]);
+                    fy = add2(uy, cb[j]);
+                } else {
+                    const f2 tx = sub2(ux, one2);
+                    fx = fma2(cc[j], uy, fma2(ca[j], tx, one2));   // 1 + px tx - py ty
+                    fy = fma2(ca[j], uy, mul2(cb[j], tx));         // px ty + py tx
+                }
+                if (j == 0) {
+                    Rx = fx; Ry = fy;
+                } else {
+                    const f2 nx = sub2(mul2(Rx, fx), mul2(Ry, fy));
+                    Ry = fma2(Rx, fy, mul2(Ry, fx));
+                    Rx = nx;
+                }
+            }
+            // even x odd, then mantissa / exponent
+            float x = f2_lo(Rx) * f2_hi(Rx) - f2_lo(Ry) * f2_hi(Ry);
+            float y = f2_lo(Rx) * f2_hi(Ry) + f2_lo(Ry) * f2_hi(Rx);
+            re[q] = nrm(x, y);
+            rx[q] = x;
+            ry[q] = y;
+        }
+        // butterfly product-reduce-scatter: lane gl ends with entry gl's product
+#pragma unroll
+        for (int lev = 0; lev < 3; ++lev) {
+            const int o = 4 >> lev;          // lane distance 4, 2, 1
+            const int cnt = 4 >> lev;        // entries exchanged
+            const bool upper = (gl & o) != 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < cnt) {
+                    // keep slot q (lower lanes keep the low half), send the other
+                    const float sx = upper ? rx[q] : rx[q + cnt];
+                    const float sy = upper ? ry[q] : ry[q + cnt];
+                    const int se = upper ? re[q] : re[q + cnt];
+                    const float kx = upper ? rx[q + cnt] : rx[q];
+                    const float ky = upper ? ry[q + cnt] : ry[q];
+                    const int ke = upper ? re[q + cnt] : re[q];
+                    const float gx = __shfl_xor_sync(0xffffffffu, sx, o);
+                    const float gy = __shfl_xor_sync(0xffffffffu, sy, o);
+                    const int ge = __shfl_xor_sync(0xffffffffu, se, o);
+                    rx[q] = kx * gx - ky * gy;
+                    ry[q] = kx * gy + ky * gx;
+                    re[q] = ke + ge;
+                }
+            }
+        }
+        if (e < naa) {
+            const float vx = rx[0] * pre.x - ry[0] * pre.y, vy = rx[0] * pre.y + ry[0] * pre.x;
+            const int d = re[0] + pre.e + eref;
+            if (d > -100 && d < 100) {
+                const float f = __uint_as_float((uint32_t)(d + 127) << 23);
+                accx = fmaf(f, vx, accx);
+                accy = fmaf(f, vy, accy);
+            } else {
+                const double f = pow2i<double>(d);
+                Ox += f * (double)vx;
+                Oy += f * (double)vy;
+            }
+        }
+    }
 }
 
 template <int NP>
@@ -53,17 +160,21 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
     const int NB = md.nbonds, K = md.K, MH = ea.MH, N = md.N, M = md.M;
     float4 *tps = reinterpret_cast<float4 *>(smem);                                      // [K][2][NB][MH]
     sc<float> *eps = reinterpret_cast<sc<float> *>(tps + (size_t)K * 2 * NB * MH);      // [K][2][NB]
-    sc<float> *acc = eps + (size_t)K * 2 * NB;                                          // [warps][NB]
+    uint16_t *gbp = reinterpret_cast<uint16_t *>(eps + (size_t)K * 2 * NB);            // [groups][NB]
+    uint8_t *gperm = reinterpret_cast<uint8_t *>(gbp + (size_t)(blockDim.x / kEfGL) * NB);   // [groups][N]
     __shared__ float s_sm[kMaxN];
     __shared__ int8_t s8[kMaxN];
     __shared__ uint16_t aa[4 * kMaxN];   // anti-aligned bond | (s_i > 0) << 15
     __shared__ int n_aa;
     __shared__ float diag_sh;
-    __shared__ sc<float> wsum[32];
+    __shared__ sc<double> gsum[2][kEfMaxThreads / kEfGL];   // per row group: sum of w_t P_t A_t, sum of w_t
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int grp = lane / kEfGL, gl = lane % kEfGL;
+    const int grp = lane / kEfGL, gl = lane % kEfGL, gbase = grp * kEfGL;
     const int gidx = warp * NG + grp, ngroups = nwarps * NG;
+    uint8_t *pgs = gperm + (size_t)gidx * N;
+    uint16_t *bps = gbp + (size_t)gidx * NB;
+    const f2 zero2 = 0, mone2 = f2_pack(-1.f, -1.f);
 
     // tables into shared memory (once per CTA)
     {
@@ -80,6 +191,7 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
             s_sm[i] = (float)sv;
             s8[i] = (int8_t)sv;
         }
+        for (int q = threadIdx.x; q < 2 * ngroups; q += blockDim.x) gsum[q / ngroups][q % ngroups] = sc<double>{0.0, 0.0, 0};
         __syncthreads();
         if (warp == 0) {
             float d = 0.f;
@@ -103,28 +215,25 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
         }
         __syncthreads();
         const int naa = n_aa;
-        for (int q = threadIdx.x; q < nwarps * naa; q += blockDim.x) {
-            const int wq = q / naa, e = q - wq * naa;
-            acc[wq * NB + e] = sc<float>{0.f, 0.f, 0};
-        }
-        sc<float> s0acc{0.f, 0.f, 0};   // this group's sum of row terms (lane 0 of the group)
-        __syncthreads();
 
-        // (every group of a warp takes the same number of rows, so that the
-        // warp-wide shuffles below see all lanes; groups past the last row
-        // compute row 0 and add nothing)
+        // (every group of a warp runs the same trip counts, so that the warp's
+        // shuffles see all lanes; groups past the last row run row 0 and add
+        // nothing)
         for (int rbase = 0; rbase < K * md.G; rbase += ngroups) {
             const bool active = rbase + gidx < K * md.G;
             const int row = active ? rbase + gidx : 0;
             const int r = row / md.G, g = row - r * md.G;
-            const uint8_t *pg = md.perm + (size_t)g * N;
+            __syncwarp();
+            for (int i = gl; i < N; i += kEfGL) pgs[i] = md.perm[(size_t)g * N + i];
+            for (int b = gl; b < NB; b += kEfGL) bps[b] = md.bperm[(size_t)g * NB + b];
+            __syncwarp();
             // ---- theta' = W_r T_g s for the lane's units (pairs k = gl + 8 j) ----
             float tx[2 * NP], ty[2 * NP];
 #pragma unroll
             for (int u = 0; u < 2 * NP; ++u) { tx[u] = 0.f; ty[u] = 0.f; }
             const cx<float> *Wr = md.Wt + (size_t)r * N * M;
             for (int i = 0; i < N; ++i) {
-                const cx<float> *wk = Wr + (size_t)pg[i] * M;
+                const cx<float> *wk = Wr + (size_t)pgs[i] * M;
                 const float si = s_sm[i];
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
@@ -142,7 +251,7 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
             cx<float> at{0.f, 0.f};
             if (md.use_bias) {
                 const cx<float> *ar = md.avec + (size_t)r * N;
-                for (int i = gl; i < N; i += kEfGL) { const cx<float> a = ar[pg[i]]; at.x += s_sm[i] * a.x; at.y += s_sm[i] * a.y; }
+                for (int i = gl; i < N; i += kEfGL) { const cx<float> a = ar[pgs[i]]; at.x += s_sm[i] * a.x; at.y += s_sm[i] * a.y; }
 #pragma unroll
                 for (int o = kEfGL / 2; o > 0; o >>= 1) {
                     at.x += __shfl_xor_sync(0xffffffffu, at.x, o);
@@ -151,9 +260,11 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
             }
             for (int sg = 0; sg < md.nsign; ++sg) {
                 const float sign = sg ? -1.f : 1.f;
-                // ---- p of the lane's units (packed pairs) and the row term ----
-                f2 px[NP], py[NP], npy[NP];
+                // ---- p of the lane's units, q = 1/p - 1, the p product and the row term ----
+                f2 ca[NP], cb[NP], cc[NP];
                 sc<float> prod{1.f, 0.f, 0};
+                f2 Px = 0, Py = 0;
+                bool small = ea.plain != 0;   // some |p| < 2^-12: the plain factors for this row
                 const cx<float> *br = md.bvec + (size_t)r * M;
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
@@ -171,152 +282,102 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
                             pxv[h] = pv.x; pyv[h] = pv.y;
                             const cx<float> q = cmul(mk(prod.x, prod.y), mant);
                             prod = sc<float>{q.x, q.y, prod.e + k};
+                            small = small || !(pv.x * pv.x + pv.y * pv.y >= 0x1p-24f);
                         }
                     }
-                    px[j] = f2_pack(pxv[0], pxv[1]);
-                    py[j] = f2_pack(pyv[0], pyv[1]);
-                    npy[j] = f2_pack(-pyv[0], -pyv[1]);
+                    // units past M: p = 1, q = 0 (their U is 1)
+                    const int m0 = 2 * (gl + kEfGL * j);
+                    if (m0 >= M) { pxv[0] = 1.f; pyv[0] = 0.f; }
+                    if (m0 + 1 >= M) { pxv[1] = 1.f; pyv[1] = 0.f; }
+                    const f2 px = f2_pack(pxv[0], pxv[1]), py = f2_pack(pyv[0], pyv[1]);
+                    const f2 pden = fma2(px, px, mul2(py, py));
+                    const f2 inv = f2_pack(__frcp_rn(f2_lo(pden)), __frcp_rn(f2_hi(pden)));
+                    const f2 qx = fma2(px, inv, mone2), qy = mul2(sub2(zero2, py), inv);   // q = 1/p - 1
+                    const f2 pfx = px, pfy = py;
+                    if (j == 0) {
+                        Px = pfx; Py = pfy;
+                    } else {
+                        const f2 nx = sub2(mul2(Px, pfx), mul2(Py, pfy));
+                        Py = fma2(Px, pfy, mul2(Py, pfx));
+                        Px = nx;
+                    }
+                    ca[j] = qx; cb[j] = qy;
                 }
-                prod = sc_norm(prod);
-#pragma unroll
-                for (int o = kEfGL / 2; o > 0; o >>= 1) {
-                    const sc<float> v{__shfl_xor_sync(0xffffffffu, prod.x, o), __shfl_xor_sync(0xffffffffu, prod.y, o),
-                                      __shfl_xor_sync(0xffffffffu, prod.e, o)};
-                    prod = sc_mul(prod, v);
-                }
+                prod = group_prod<kEfGL>(prod);
                 const cx<float> lc = md.logc[r];
                 sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
-                float c = md.chi[g];
-                if (sg && md.chiP < 0) c = -c;
-                lead.x *= c; lead.y *= c;
+                float chg = md.chi[g];
+                if (sg && md.chiP < 0) chg = -chg;
+                lead.x *= chg; lead.y *= chg;
                 const sc<float> wt = sc_mul(prod, sc_norm(lead));   // the row term (same in every lane)
-                if (gl == 0 && active) s0acc = sc_add(s0acc, wt);
+                if (gl == 0 && active) gsum[1][gidx] = sc_add(gsum[1][gidx], sc<double>{(double)wt.x, (double)wt.y, wt.e});
 
-                const f2 one2 = f2_pack(1.f, 1.f);
-                // ---- entries, 8 at a time ----
-                for (int e0 = 0; e0 < naa; e0 += kEfGL) {
-                    // lane gl: table offset and prefactor of entry e0 + gl
-                    const int e = e0 + gl;
-                    int off = 0;
-                    sc<float> pre{0.f, 0.f, 0};
-                    if (e < naa) {
-                        const uint16_t code = aa[e];
-                        const int b = code & 0x7fff;
-                        const uint16_t bp = md.bperm[(size_t)g * NB + b];
-                        const int bb = bp & 0x7fff;
-                        // orientation of the exchange on the image bond, for this sign
-                        const bool pos = ((code >> 15) != 0) != ((bp >> 15) != 0);   // s_i flip-corrected
-                        const int o = (pos != (sg != 0)) ? 0 : 1;
-                        off = ((r * 2 + o) * NB + bb) * MH;
-                        pre = eps[(r * 2 + o) * NB + bb];
-                    }
-                    float rx[kEfGL], ry[kEfGL];
-                    int re[kEfGL];
+                float accx = 0.f, accy = 0.f;
+                double Ox = 0.0, Oy = 0.0;
+                sc<float> mult;
+                if (!__any_sync(0xffffffffu, small)) {
+                    const float u = f2_lo(Px) * f2_hi(Px) - f2_lo(Py) * f2_hi(Py);
+                    const float v = f2_lo(Px) * f2_hi(Py) + f2_lo(Py) * f2_hi(Px);
+                    const sc<float> Pp = group_prod<kEfGL>(sc<float>{u, v, 0});
+                    ef_entries<NP, true>(md, tps, eps, aa, bps, naa, r, sg, MH, ca, cb, cc, Pp.e, gl, gbase, accx, accy,
+                                         Ox, Oy);
+                    mult = sc_mul(wt, sc<float>{Pp.x, Pp.y, 0});
+                } else {
+                    // p again, for the plain factors
 #pragma unroll
-                    for (int q = 0; q < kEfGL; ++q) {
-                        const int oq = __shfl_sync(0xffffffffu, off, grp * kEfGL + q);
-                        const float4 *trow = tps + oq;
-                        // running products of the even and odd units (packed)
-                        f2 Rx = one2, Ry = 0;
+                    for (int j = 0; j < NP; ++j) {
+                        float pxv[2], pyv[2];
 #pragma unroll
-                        for (int j = 0; j < NP; ++j) {
-                            f2 tx2, ty2;
-                            lds128(trow + gl + kEfGL * j, tx2, ty2);
-                            const f2 fx = fma2(npy[j], ty2, fma2(px[j], tx2, one2));   // 1 + px tx - py ty
-                            const f2 fy = fma2(py[j], tx2, mul2(px[j], ty2));           // px ty + py tx
-                            if (j == 0) {
-                                Rx = fx; Ry = fy;
-                            } else {
-                                const f2 nx = sub2(mul2(Rx, fx), mul2(Ry, fy));
-                                Ry = fma2(Rx, fy, mul2(Ry, fx));
-                                Rx = nx;
+                        for (int h = 0; h < 2; ++h) {
+                            const int m = 2 * (gl + kEfGL * j) + h;
+                            pxv[h] = 0.f; pyv[h] = 0.f;
+                            if (m < M) {
+                                cx<float> th{sign * tx[2 * j + h], sign * ty[2 * j + h]};
+                                if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
+                                cx<float> mant, pv;
+                                int k;
+                                cosh2(th, mant, k, pv);
+                                pxv[h] = pv.x; pyv[h] = pv.y;
                             }
                         }
-                        // even x odd, then mantissa / exponent
-                        float x = f2_lo(Rx) * f2_hi(Rx) - f2_lo(Ry) * f2_hi(Ry);
-                        float y = f2_lo(Rx) * f2_hi(Ry) + f2_lo(Ry) * f2_hi(Rx);
-                        const int ex = expo<float>(x, y);
-                        const float s = pow2i<float>(-ex);
-                        rx[q] = x * s; ry[q] = y * s; re[q] = ex;
+                        ca[j] = f2_pack(pxv[0], pxv[1]);
+                        cb[j] = f2_pack(pyv[0], pyv[1]);
+                        cc[j] = f2_pack(-pyv[0], -pyv[1]);
                     }
-                    // butterfly product-reduce-scatter: lane gl ends with entry gl's product
-#pragma unroll
-                    for (int lev = 0; lev < 3; ++lev) {
-                        const int o = 4 >> lev;          // lane distance 4, 2, 1
-                        const int cnt = 4 >> lev;        // entries exchanged
-                        const bool upper = (gl & o) != 0;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (q < cnt) {
-                                // keep slot q (lower lanes keep the low half), send the other
-                                const float sx = upper ? rx[q] : rx[q + cnt];
-                                const float sy = upper ? ry[q] : ry[q + cnt];
-                                const int se = upper ? re[q] : re[q + cnt];
-                                const float kx = upper ? rx[q + cnt] : rx[q];
-                                const float ky = upper ? ry[q + cnt] : ry[q];
-                                const int ke = upper ? re[q + cnt] : re[q];
-                                const float gx = __shfl_xor_sync(0xffffffffu, sx, o);
-                                const float gy = __shfl_xor_sync(0xffffffffu, sy, o);
-                                const int ge = __shfl_xor_sync(0xffffffffu, se, o);
-                                float nx = kx, ny = ky;
-                                int ne = ke;
-                                scm(nx, ny, ne, gx, gy, ge);
-                                rx[q] = nx; ry[q] = ny; re[q] = ne;
-                            }
-                        }
-                    }
-                    // lane gl: entry e0 + gl (the kept slot 0), times prefactor and row term
-                    sc<float> v{0.f, 0.f, 0};
-                    if (e < naa && active) v = sc_mul(sc_mul(sc_norm(sc<float>{rx[0], ry[0], re[0]}), pre), wt);
-                    // sum over the warp's groups (they hold the same entries), then into the warp's sums
-#pragma unroll
-                    for (int o = kEfGL; o < 32; o <<= 1) {
-                        const sc<float> u{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
-                                          __shfl_xor_sync(0xffffffffu, v.e, o)};
-                        v = sc_add(v, u);
-                    }
-                    if (grp == 0 && e < naa) acc[warp * NB + e] = sc_add(acc[warp * NB + e], v);
+                    ef_entries<NP, false>(md, tps, eps, aa, bps, naa, r, sg, MH, ca, cb, cc, 0, gl, gbase, accx, accy,
+                                          Ox, Oy);
+                    mult = wt;
                 }
+                double ax = (double)accx + Ox, ay = (double)accy + Oy;
+#pragma unroll
+                for (int o = kEfGL / 2; o > 0; o >>= 1) {
+                    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                }
+                if (gl == 0 && active) gsum[0][gidx] = sc_add(gsum[0][gidx], sd_mul(mult, ax, ay));
             }
         }
-        // ---- the sum of all row terms (lane 0 of each group holds its part) ----
-#pragma unroll
-        for (int o = kEfGL; o < 32; o <<= 1) {
-            const sc<float> u{__shfl_xor_sync(0xffffffffu, s0acc.x, o), __shfl_xor_sync(0xffffffffu, s0acc.y, o),
-                              __shfl_xor_sync(0xffffffffu, s0acc.e, o)};
-            s0acc = sc_add(s0acc, u);
-        }
-        if (lane == 0) wsum[warp] = s0acc;
         __syncthreads();
-        if (warp == 0) {
-            sc<float> tot{0.f, 0.f, 0};
-            if (lane == 0)
-                for (int q = 0; q < nwarps; ++q) tot = sc_add(tot, wsum[q]);
-            const sc<float> S0{__shfl_sync(0xffffffffu, tot.x, 0), __shfl_sync(0xffffffffu, tot.y, 0),
-                               __shfl_sync(0xffffffffu, tot.e, 0)};
-            double hx = 0.0, hy = 0.0;
-            for (int e = lane; e < naa; e += 32) {
-                sc<float> se = acc[e];
-                for (int q = 1; q < nwarps; ++q) se = sc_add(se, acc[q * NB + e]);
-                if (!sc_zero(se)) {
-                    const double f = ldexp(1.0, se.e - S0.e);
-                    const double ax = (double)se.x, ay = (double)se.y, bx = (double)S0.x, by = (double)S0.y;
-                    const double den = bx * bx + by * by;
-                    const double Rx = (ax * bx + ay * by) / den * f, Ry = (ay * bx - ax * by) / den * f;
-                    const double c1 = 0.5 * (double)bondJ(md, aa[e] & 0x7fff);
-                    hx += c1 * Rx;
-                    hy += c1 * Ry;
-                }
-            }
+        if (warp == 0) {   // the groups' sums, a tree over the lanes of warp 0
+            sc<double> t1{0.0, 0.0, 0}, t0{0.0, 0.0, 0};
+            for (int q = lane; q < ngroups; q += 32) { t1 = sc_add(t1, gsum[0][q]); t0 = sc_add(t0, gsum[1][q]); }
+#pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                hx += __shfl_xor_sync(0xffffffffu, hx, o);
-                hy += __shfl_xor_sync(0xffffffffu, hy, o);
+                const sc<double> u1{__shfl_xor_sync(0xffffffffu, t1.x, o), __shfl_xor_sync(0xffffffffu, t1.y, o),
+                                    __shfl_xor_sync(0xffffffffu, t1.e, o)};
+                const sc<double> u0{__shfl_xor_sync(0xffffffffu, t0.x, o), __shfl_xor_sync(0xffffffffu, t0.y, o),
+                                    __shfl_xor_sync(0xffffffffu, t0.e, o)};
+                t1 = sc_add(t1, u1);
+                t0 = sc_add(t0, u0);
             }
             if (lane == 0) {
-                const double h1x = (double)diag_sh + hx;
-                if (!sc_finite(S0) || sc_zero(S0) || !isfinite(h1x) || !isfinite(hy)) flag_range(md.status);
+                const double den = t0.x * t0.x + t0.y * t0.y;
+                const double f = ldexp(1.0, t1.e - t0.e);
+                const double rx = (t1.x * t0.x + t1.y * t0.y) / den * f, ry = (t1.y * t0.x - t1.x * t0.y) / den * f;
+                const double h1x = (double)diag_sh + rx;
+                if (sc_zero(t0) || !isfinite(h1x) || !isfinite(ry)) flag_range(md.status);
                 h1_out[2 * smp] = h1x;
-                h1_out[2 * smp + 1] = hy;
+                h1_out[2 * smp + 1] = ry;
             }
         }
         __syncthreads();
@@ -324,8 +385,8 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
 }
 
 // Paired tables from the connection tables of the model: tp[(r 2 + o) NB + b][k]
-// = (Tx_2k, Tx_2k+1, Ty_2k, Ty_2k+1) for unit pairs k < MH (T = 0 past M), and
-// ep = e^{(1 - 2 o) C_b} as scaled numbers.
+// = (Ux_2k, Ux_2k+1, Uy_2k, Uy_2k+1), U = 1 + T, for unit pairs k < MH (U = 1
+// past M), and ep = e^{(1 - 2 o) C_b} as scaled numbers.
 __global__ void k_tables_paired(DevModel<float> md, int MH, float4 *__restrict__ tp, sc<float> *__restrict__ ep)
 {
     const int NB = md.nbonds;
@@ -337,7 +398,7 @@ __global__ void k_tables_paired(DevModel<float> md, int MH, float4 *__restrict__
         const int m0 = 2 * k, m1 = 2 * k + 1;
         const cx<float> a = m0 < md.M ? src[m0] : cx<float>{0.f, 0.f};
         const cx<float> b = m1 < md.M ? src[m1] : cx<float>{0.f, 0.f};
-        tp[q] = make_float4(a.x, b.x, a.y, b.y);
+        tp[q] = make_float4(1.f + a.x, 1.f + b.x, a.y, b.y);
     }
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)md.K * 2 * NB;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -354,11 +415,13 @@ __global__ void k_tables_paired(DevModel<float> md, int MH, float4 *__restrict__
 // ---------------------------------------------------------------------------
 static int ef_np(int M) { return (M + 2 * kEfGL - 1) / (2 * kEfGL); }   // unit pairs per lane
 
+// tables, prefactors and the per-group images of the bonds and sites under
+// the group's row
 static size_t ef_smem(const DevModel<float> &md, int warps)
 {
     const int MH = kEfGL * ef_np(md.M);
     return (size_t)md.K * 2 * md.nbonds * MH * sizeof(float4) + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) +
-           (size_t)warps * md.nbonds * sizeof(sc<float>);
+           (size_t)warps * (32 / kEfGL) * (md.nbonds * sizeof(uint16_t) + md.N);
 }
 
 static int ef_warps(const DevModel<float> &md)
@@ -408,6 +471,10 @@ cudaError_t launch_eloc_fast(const DevModel<float> &md, const void *tables, cons
     ea.tp = reinterpret_cast<const float4 *>(tables);
     ea.ep = reinterpret_cast<const sc<float> *>(ea.tp + (size_t)md.K * 2 * md.nbonds * ea.MH);
     ea.warps = ef_warps(md);
+    // Test hook (unset in normal use): NNQS_TEST_ELOC_PLAIN=1 takes the plain
+    // factors 1 + p (U - 1) in every row.
+    const char *hook = getenv("NNQS_TEST_ELOC_PLAIN");
+    ea.plain = hook && hook[0] == '1';
     const size_t smem = ef_smem(md, ea.warps);
     const int grid = (int)(n < nsm ? n : nsm);
     void (*kern)(DevModel<float>, EfArgs, const uint64_t *, int64_t, double *) = nullptr;

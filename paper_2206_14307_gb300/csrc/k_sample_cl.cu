@@ -86,12 +86,17 @@ struct ClPlan {
     size_t smem;   // dynamic shared memory per CTA
 };
 
+// rows (r, g) of the projected sum that a CTA's TP pairs touch
+__host__ __device__ __forceinline__ int cl_rows(const DevModel<float> &md, int TP) { return TP / md.nsign + 2; }
+
 // shared memory of one CTA: site tables [K][2][N][M], p [TP][M], terms, new
-// terms and pair products [TP], exchange slots [2][CL][8]
+// terms and pair products [TP], site prefactors [K][2][N], exchange slots
+// [2][CL][8], images of the sites under the CTA's rows [rows][N]
 static size_t cl_smem(const DevModel<float> &md, int TP, int CL)
 {
     return (size_t)md.K * 2 * md.N * md.M * sizeof(cx<float>) + (size_t)TP * md.M * sizeof(cx<float>) +
-           3 * (size_t)TP * sizeof(sc<float>) + 2 * (size_t)CL * 8 * sizeof(float);
+           3 * (size_t)TP * sizeof(sc<float>) + (size_t)md.K * 2 * md.N * sizeof(sc<float>) +
+           2 * (size_t)CL * 8 * sizeof(float) + (size_t)cl_rows(md, TP) * md.N;
 }
 
 // Sums over the warp of two scaled complex numbers: v = (sum a, sum b) as plain
@@ -155,7 +160,9 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     sc<float> *term = reinterpret_cast<sc<float> *>(pc + (size_t)TP * M);        // [TP]
     sc<float> *nterm = term + TP;                                               // [TP] new terms of the last proposal
     sc<float> *gprod = nterm + TP;                                              // [TP] pair products of the proposal
-    float *xch = reinterpret_cast<float *>(gprod + TP);                         // [2][CL][8]
+    sc<float> *es = gprod + TP;                                                 // [K][2][N] site prefactors
+    float *xch = reinterpret_cast<float *>(es + (size_t)md.K * 2 * N);           // [2][CL][8]
+    uint8_t *prow = reinterpret_cast<uint8_t *>(xch + 2 * CL * 8);              // [rows][N] images of the sites
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int grp = lane / kCGL, gl = lane % kCGL;
@@ -165,9 +172,15 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     const int t0 = (int)rank * TP;
     const int ntp = t0 >= nrs ? 0 : (nrs - t0 < TP ? nrs - t0 : TP);
     uint32_t gstep = 0;   // steps of this cluster over all its chains (parity of the exchange slots)
+    const int row0 = t0 / md.nsign;   // first row (r, g) of this CTA's pairs
     for (int q = threadIdx.x; q < md.K * 2 * N * M; q += blockDim.x) {
         const int m = q % M, row = q / M;   // row = (r * 2 + half) * N + k
         s4[q] = md.S4[(size_t)row * md.Mp + m];
+    }
+    for (int q = threadIdx.x; q < md.K * 2 * N; q += blockDim.x) es[q] = md.ES[q];
+    for (int q = threadIdx.x; q < cl_rows(md, TP) * N; q += blockDim.x) {
+        const int rw = row0 + q / N, i = q - (q / N) * N;
+        if (rw < md.K * md.G) prow[q] = md.perm[(size_t)(rw % md.G) * N + i];
     }
     __syncthreads();
 
@@ -286,11 +299,12 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 const int t = t0 + tl;
                 const int row = md.nsign == 2 ? t >> 1 : t;
                 const int sg = t - row * md.nsign;
-                const int r = row / md.G, g = row - r * md.G;
-                const uint8_t *pg = md.perm + (size_t)g * N;
+                const int r = row / md.G;
+                const uint8_t *pg = prow + (size_t)(row - row0) * N;
+                const int ku = pg[iu], kd = pg[id];
                 const size_t rs = (size_t)r * 2 * N * M;
-                const cx<float> *Su = s4 + rs + ((size_t)sg * N + pg[iu]) * M;         // exp(-4 sigma W_u)
-                const cx<float> *Sd = s4 + rs + ((size_t)(sg ^ 1) * N + pg[id]) * M;   // exp(+4 sigma W_d)
+                const cx<float> *Su = s4 + rs + ((size_t)sg * N + ku) * M;         // exp(-4 sigma W_u)
+                const cx<float> *Sd = s4 + rs + ((size_t)(sg ^ 1) * N + kd) * M;   // exp(+4 sigma W_d)
                 const cx<float> *Pu = s4 + rs + ((size_t)sg * N + pg[pu]) * M;
                 const cx<float> *Pd = s4 + rs + ((size_t)(sg ^ 1) * N + pg[pd]) * M;
                 cx<float> *pr = pc + (size_t)tl * M;
@@ -332,13 +346,17 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 const int t = t0 + tl;
                 const int row = md.nsign == 2 ? t >> 1 : t;
                 const int sg = t - row * md.nsign;
-                const int r = row / md.G, g = row - r * md.G;
-                const int ku = md.perm[(size_t)g * N + iu], kd = md.perm[(size_t)g * N + id];
-                const sc<float> *ESr = md.ES + (size_t)r * 2 * N;
-                const sc<float> pref = sc_mul(ESr[(size_t)sg * N + ku], ESr[(size_t)(sg ^ 1) * N + kd]);
+                const int r = row / md.G;
+                const uint8_t *pg = prow + (size_t)(row - row0) * N;
+                const sc<float> *ESr = es + (size_t)r * 2 * N;
+                const sc<float> a = ESr[(size_t)sg * N + pg[iu]], b = ESr[(size_t)(sg ^ 1) * N + pg[id]];
+                const sc<float> gp = gprod[tl];
                 sc<float> old = term[tl];
                 if (pending) { old = nterm[tl]; term[tl] = old; }
-                const sc<float> tn = sc_mul(sc_mul(old, gprod[tl]), pref);
+                // new term = old x pair product x prefactor (mantissas in [1, 2): one normalisation)
+                cx<float> m = cmul(cmul(mk(old.x, old.y), mk(gp.x, gp.y)), cmul(mk(a.x, a.y), mk(b.x, b.y)));
+                const int e = old.e + gp.e + a.e + b.e + nrm(m.x, m.y);
+                const sc<float> tn{m.x, m.y, e};
                 nterm[tl] = tn;
                 so = sc_add(so, old);
                 sn = sc_add(sn, tn);
