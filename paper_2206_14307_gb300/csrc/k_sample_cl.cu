@@ -18,6 +18,7 @@
 // the next step's pass, so no speculative second buffer is needed and p is
 // read once per step.
 #include "common.cuh"
+#include "f2.cuh"
 #include "kernels.h"
 
 namespace nnqs {
@@ -86,17 +87,15 @@ struct ClPlan {
     size_t smem;   // dynamic shared memory per CTA
 };
 
-// rows (r, g) of the projected sum that a CTA's TP pairs touch
-__host__ __device__ __forceinline__ int cl_rows(const DevModel<float> &md, int TP) { return TP / md.nsign + 2; }
-
-// shared memory of one CTA: site tables [K][2][N][M], p [TP][M], terms, new
-// terms and pair products [TP], site prefactors [K][2][N], exchange slots
-// [2][CL][8], images of the sites under the CTA's rows [rows][N]
-static size_t cl_smem(const DevModel<float> &md, int TP, int CL)
+// Shared memory of one CTA: site factor rows u = exp(-+4W) [K][2][N] and the
+// chain's q rows [TP] (64 MPL bytes a row, see below), per pair the term,
+// term x prod_m p_m and their values after an accepted proposal, site
+// prefactors e^{+-Cs} and the products of u over the units e^{-+4 CS}
+// [K][2][N] each, exchange slots [2][CL][8], a flag byte per pair.
+static size_t cl_smem(const DevModel<float> &md, int TP, int CL, int MPL)
 {
-    return (size_t)md.K * 2 * md.N * md.M * sizeof(cx<float>) + (size_t)TP * md.M * sizeof(cx<float>) +
-           3 * (size_t)TP * sizeof(sc<float>) + (size_t)md.K * 2 * md.N * sizeof(sc<float>) +
-           2 * (size_t)CL * 8 * sizeof(float) + (size_t)cl_rows(md, TP) * md.N;
+    return (size_t)(md.K * 2 * md.N + TP) * 64 * MPL + 4 * (size_t)TP * sizeof(sc<float>) +
+           2 * (size_t)md.K * 2 * md.N * sizeof(sc<float>) + 2 * (size_t)CL * 8 * sizeof(float) + (size_t)TP;
 }
 
 // Sums over the warp of two scaled complex numbers: v = (sum a, sum b) as plain
@@ -114,6 +113,15 @@ __device__ __forceinline__ int warp_scaled(sc<float> a, sc<float> b, float (&v)[
     return e;
 }
 
+// units per lane of a width M (the kernel's variants)
+static int cl_mpl(int M)
+{
+    const int need = (M + kCGL - 1) / kCGL;
+    return need <= 2 ? 2 : need <= 4 ? 4 : need <= 9 ? 9 : 16;
+}
+
+constexpr size_t kClSmemLimit = 224 * 1024;   // dynamic shared memory of one CTA (static part below 3 KB)
+
 // The smallest cluster whose CTAs hold the chain's cache; CL = 0 if none does.
 static ClPlan cl_plan(const DevModel<float> &md, int force_cl)
 {
@@ -122,8 +130,8 @@ static ClPlan cl_plan(const DevModel<float> &md, int force_cl)
     for (int CL = 1; CL <= 8; CL *= 2) {
         if (force_cl > 0 && CL != force_cl) continue;
         const int TP = (nrs + CL - 1) / CL;
-        const size_t s = cl_smem(md, TP, CL);
-        if (s <= 220 * 1024) {
+        const size_t s = cl_smem(md, TP, CL, cl_mpl(md.M));
+        if (s <= kClSmemLimit) {
             p.CL = CL; p.TP = TP; p.smem = s;
             break;
         }
@@ -140,12 +148,44 @@ static ClPlan cl_plan(const DevModel<float> &md, int force_cl)
     return p;
 }
 
+// Row layout of the site factor rows and the chain's q rows: lane gl of a
+// pair group owns the units m = gl + 8 j (j < MPL); the units (j, j + 1) of
+// even j < MPL - 1 sit in one float4 (x_j, x_j+1, y_j, y_j+1) at float4 index
+// (j / 2) 8 + gl, so that a group reads 128 contiguous bytes per step; for odd
+// MPL the last unit is a float2 at float2 index (MPL - 1) 8 + gl.  A row is
+// 8 MPL complex numbers (64 MPL bytes).
+template <int MPL> __device__ __forceinline__ void row_offsets(int j, int gl, int &ore, int &oim)
+{
+    if (j < MPL - (MPL & 1)) {
+        const int base = ((j >> 1) * 8 + gl) * 4;
+        ore = base + (j & 1);
+        oim = base + 2 + (j & 1);
+    } else {
+        const int base = ((MPL - 1) * 8 + gl) * 2;
+        ore = base;
+        oim = base + 1;
+    }
+}
+
+__device__ __forceinline__ void lds64(const void *p, float &x, float &y)
+{
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(addr));
+}
+__device__ __forceinline__ void sts128(void *p, f2 a, f2 b)
+{
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
+}
+
 template <int MPL>
 __global__ void __launch_bounds__(kClMaxThreads, 1)
     k_sample_cl(DevModel<float> md, uint64_t seed, int n_chains, int n_per_chain, int n_skip, int n_burn,
                 uint64_t *__restrict__ cfg_out, float *__restrict__ acc_out, int CL, int TP)
 {
     constexpr int NG = 32 / kCGL;
+    constexpr int NPAIR = MPL / 2, SGL = MPL & 1;
+    constexpr int RF4 = 4 * MPL;   // float4 per row
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_sm[kMaxN];
     __shared__ uint64_t upm[kMaxWords], dnm[kMaxWords];
@@ -155,32 +195,45 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     __shared__ float u_sh;
 
     const int M = md.M, N = md.N;
-    cx<float> *s4 = reinterpret_cast<cx<float> *>(smem);                        // [K][2][N][M] exp(-+4W)
-    cx<float> *pc = s4 + (size_t)md.K * 2 * N * M;                              // [TP][M]
-    sc<float> *term = reinterpret_cast<sc<float> *>(pc + (size_t)TP * M);        // [TP]
-    sc<float> *nterm = term + TP;                                               // [TP] new terms of the last proposal
-    sc<float> *gprod = nterm + TP;                                              // [TP] pair products of the proposal
-    sc<float> *es = gprod + TP;                                                 // [K][2][N] site prefactors
-    float *xch = reinterpret_cast<float *>(es + (size_t)md.K * 2 * N);           // [2][CL][8]
-    uint8_t *prow = reinterpret_cast<uint8_t *>(xch + 2 * CL * 8);              // [rows][N] images of the sites
+    float4 *s4 = reinterpret_cast<float4 *>(smem);                              // [K][2][N] rows of u = exp(-+4W)
+    float4 *qc = s4 + (size_t)md.K * 2 * N * RF4;                               // [TP] rows of q = (1 - p)/p
+    sc<float> *term = reinterpret_cast<sc<float> *>(qc + (size_t)TP * RF4);     // [TP] the pair's term
+    sc<float> *tpr = term + TP;                                                 // [TP] term x prod_m p_m
+    sc<float> *nterm = tpr + TP;                                                // [TP] prod (q + U), then the new term
+    sc<float> *ntpr = nterm + TP;                                               // [TP] tpr after an accepted proposal
+    sc<float> *es = ntpr + TP;                                                  // [K][2][N] site prefactors e^{+-Cs}
+    sc<float> *ec = es + (size_t)md.K * 2 * N;                                  // [K][2][N] prod_m u_m = e^{-+4 CS}
+    float *xch = reinterpret_cast<float *>(ec + (size_t)md.K * 2 * N);          // [2][CL][8]
+    // [TP] per pair: some |q| of the pair may exceed 2^12, so that its running
+    // products are renormalised after every unit pair
+    uint8_t *bigf = reinterpret_cast<uint8_t *>(xch + 2 * CL * 8);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int grp = lane / kCGL, gl = lane % kCGL;
+    const int grp = lane / kCGL, gl = lane % kCGL, gbase = grp * kCGL;
     const int slot = warp * NG + grp, nslots = nwarps * NG;
     const int nrs = md.K * md.G * md.nsign;
     const uint32_t rank = cluster_rank();
     const int t0 = (int)rank * TP;
     const int ntp = t0 >= nrs ? 0 : (nrs - t0 < TP ? nrs - t0 : TP);
     uint32_t gstep = 0;   // steps of this cluster over all its chains (parity of the exchange slots)
-    const int row0 = t0 / md.nsign;   // first row (r, g) of this CTA's pairs
-    for (int q = threadIdx.x; q < md.K * 2 * N * M; q += blockDim.x) {
-        const int m = q % M, row = q / M;   // row = (r * 2 + half) * N + k
-        s4[q] = md.S4[(size_t)row * md.Mp + m];
-    }
-    for (int q = threadIdx.x; q < md.K * 2 * N; q += blockDim.x) es[q] = md.ES[q];
-    for (int q = threadIdx.x; q < cl_rows(md, TP) * N; q += blockDim.x) {
-        const int rw = row0 + q / N, i = q - (q / N) * N;
-        if (rw < md.K * md.G) prow[q] = md.perm[(size_t)(rw % md.G) * N + i];
+    {
+        float *s4f = reinterpret_cast<float *>(s4);
+        for (int q = threadIdx.x; q < md.K * 2 * N * 8 * MPL; q += blockDim.x) {
+            const int row = q / (8 * MPL), w = q - row * 8 * MPL;   // row = (r * 2 + half) * N + k
+            const int l = w % 8, j = w / 8, m = l + 8 * j;
+            const cx<float> v = m < M ? md.S4[(size_t)row * md.Mp + m] : cx<float>{1.f, 0.f};
+            int ore, oim;
+            row_offsets<MPL>(j, l, ore, oim);
+            s4f[(size_t)row * 8 * MPL * 2 + ore] = v.x;
+            s4f[(size_t)row * 8 * MPL * 2 + oim] = v.y;
+        }
+        for (int q = threadIdx.x; q < md.K * 2 * N; q += blockDim.x) {
+            es[q] = md.ES[q];
+            const int rk = q / (2 * N), o = (q / N) & 1, k = q % N;
+            const cx<float> c = md.CS[(size_t)rk * N + k];
+            const float f = o ? 4.f : -4.f;
+            ec[q] = sc_norm(sc_exp(cx<float>{f * c.x, f * c.y}));
+        }
     }
     __syncthreads();
 
@@ -207,7 +260,8 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
         }
         __syncthreads();
 
-        // ---- fresh cache of this CTA's pairs ----
+        // ---- fresh cache of this CTA's pairs: q = 1/p - 1 per unit, the term
+        //      and term x prod_m p_m per pair ----
         for (int tb = 0; tb < ntp; tb += nslots) {
             const int tl0 = tb + slot;
             const bool active = tl0 < ntp;
@@ -238,35 +292,49 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
 #pragma unroll
                 for (int o = kCGL / 2; o > 0; o >>= 1) { at.x += shfl_x(at.x, o); at.y += shfl_x(at.y, o); }
             }
-            sc<float> prod{1.f, 0.f, 0};
+            sc<float> prod{1.f, 0.f, 0}, pp{1.f, 0.f, 0};
+            bool big = false;
+            float *qf = reinterpret_cast<float *>(qc + (size_t)tl * RF4);
             const cx<float> *br = md.bvec + (size_t)r * M;
 #pragma unroll
             for (int j = 0; j < MPL; ++j) {
                 const int m = gl + kCGL * j;
+                cx<float> q{0.f, 0.f};
                 if (m < M) {
                     cx<float> th{sign * thp[j].x, sign * thp[j].y};
                     if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
                     cx<float> mant, pv;
                     int k;
                     cosh2(th, mant, k, pv);
-                    if (active) pc[(size_t)tl * M + m] = pv;
-                    const cx<float> q = cmul(mk(prod.x, prod.y), mant);
-                    prod = sc<float>{q.x, q.y, prod.e + k};
+                    const cx<float> c = cmul(mk(prod.x, prod.y), mant);
+                    prod = sc_norm(sc<float>{c.x, c.y, prod.e + k});
+                    pp = sc_mul(pp, sc<float>{pv.x, pv.y, 0});
+                    const float d = pv.x * pv.x + pv.y * pv.y;
+                    if (d > 0.f) {
+                        const float id = 1.f / d;
+                        q = cx<float>{pv.x * id - 1.f, -pv.y * id};
+                    } else {
+                        q = cx<float>{0x1p60f, 0.f};   // p = 0 (the unit's factor is 1 - p: q is not used)
+                    }
+                    big = big || !(q.x * q.x + q.y * q.y <= 0x1p24f);
                 }
+                int ore, oim;
+                row_offsets<MPL>(j, gl, ore, oim);
+                if (active) { qf[ore] = q.x; qf[oim] = q.y; }
             }
-            prod = sc_norm(prod);
-#pragma unroll
-            for (int o = kCGL / 2; o > 0; o >>= 1) {
-                const sc<float> w{shfl_x(prod.x, o), shfl_x(prod.y, o), __shfl_xor_sync(0xffffffffu, prod.e, o)};
-                prod = sc_mul(prod, w);
-            }
+            const unsigned bal = __ballot_sync(0xffffffffu, big);
+            prod = group_prod<kCGL>(prod);
+            pp = group_prod<kCGL>(pp);
             if (gl == 0 && active) {
                 const cx<float> lc = md.logc[r];
                 sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
                 float c = md.chi[g];
                 if (sign < 0 && md.chiP < 0) c = -c;
                 lead.x *= c; lead.y *= c;
-                term[tl] = sc_mul(prod, sc_norm(lead));
+                const sc<float> tm = sc_mul(prod, sc_norm(lead));
+                term[tl] = tm;
+                tpr[tl] = sc_mul(tm, pp);
+                bigf[tl] = ((bal >> gbase) & 0xffu) != 0;
             }
         }
         __syncthreads();
@@ -283,15 +351,15 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
         __syncthreads();
         for (int step = 0; step < total; ++step, ++gstep) {
             const int iu = site_u, id = site_d;
-            // the previous step's exchange, if accepted, is applied to p in this pass
+            // the previous step's exchange, if accepted, is applied to q in this pass
             const int pending = pend, pu = pend_u, pd = pend_d;
             if (threadIdx.x == 32 && step + 1 < total) {
                 // the next step's Philox words, ahead of this step's decision
                 const u32x4 w = philox((uint32_t)(step + 1), 0u, 0u, 0u, k0, k1);
                 wnext[0] = w.v[0]; wnext[1] = w.v[1]; wnext[2] = w.v[2];
             }
-            // ---- one pass: p <- p (1 + T') / (1 + p T') for a pending exchange, then
-            //      the factors 1 + p T of this proposal; each pair group's product ----
+            // ---- one pass: q <- q / U' for a pending exchange (U' its factors),
+            //      then prod_m (q_m + U_m) of this proposal per pair ----
             for (int tb = 0; tb < ntp; tb += nslots) {
                 const int tl0 = tb + slot;
                 const bool active = tl0 < ntp;
@@ -299,65 +367,120 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 const int t = t0 + tl;
                 const int row = md.nsign == 2 ? t >> 1 : t;
                 const int sg = t - row * md.nsign;
-                const int r = row / md.G;
-                const uint8_t *pg = prow + (size_t)(row - row0) * N;
-                const int ku = pg[iu], kd = pg[id];
-                const size_t rs = (size_t)r * 2 * N * M;
-                const cx<float> *Su = s4 + rs + ((size_t)sg * N + ku) * M;         // exp(-4 sigma W_u)
-                const cx<float> *Sd = s4 + rs + ((size_t)(sg ^ 1) * N + kd) * M;   // exp(+4 sigma W_d)
-                const cx<float> *Pu = s4 + rs + ((size_t)sg * N + pg[pu]) * M;
-                const cx<float> *Pd = s4 + rs + ((size_t)(sg ^ 1) * N + pg[pd]) * M;
-                cx<float> *pr = pc + (size_t)tl * M;
-                cx<float> prod{1.f, 0.f};
+                const int r = row / md.G, g = row - r * md.G;
+                const uint8_t *pg = md.perm + (size_t)g * N;
+                const int rs = r * 2 * N;
+                const float4 *Su = s4 + (size_t)(rs + sg * N + pg[iu]) * RF4 + gl;          // exp(-4 sigma W_u)
+                const float4 *Sd = s4 + (size_t)(rs + (sg ^ 1) * N + pg[id]) * RF4 + gl;    // exp(+4 sigma W_d)
+                // 1/U' of the pending exchange: the factors of the opposite orientation
+                const float4 *Vu = s4 + (size_t)(rs + (sg ^ 1) * N + pg[pu]) * RF4 + gl;
+                const float4 *Vd = s4 + (size_t)(rs + sg * N + pg[pd]) * RF4 + gl;
+                float4 *qr = qc + (size_t)tl * RF4 + gl;
+                bool big = bigf[tl] != 0;
+                f2 Rx = 0, Ry = 0;
+                int elo = 0, ehi = 0;
 #pragma unroll
-                for (int j = 0; j < MPL; ++j) {
-                    const int m = gl + kCGL * j;
-                    if (m < M) {
-                        cx<float> p = pr[m];
-                        if (pending) {
-                            const cx<float> e2 = cmul(Pu[m], Pd[m]);
-                            const cx<float> tt{e2.x - 1.f, e2.y};
-                            const cx<float> f{1.f + p.x * tt.x - p.y * tt.y, p.x * tt.y + p.y * tt.x};
-                            const cx<float> num = cmul(p, e2);
-                            const float d = rcp_nr_f(f.x * f.x + f.y * f.y);
-                            p = cx<float>{(num.x * f.x + num.y * f.y) * d, (num.y * f.x - num.x * f.y) * d};
-                            if (active) pr[m] = p;
-                        }
-                        const cx<float> e2 = cmul(Su[m], Sd[m]);   // e^{2 Delta}
-                        const cx<float> tt{e2.x - 1.f, e2.y};
-                        const cx<float> f{1.f + p.x * tt.x - p.y * tt.y, p.x * tt.y + p.y * tt.x};
-                        prod = cmul(prod, f);
+                for (int i = 0; i < NPAIR; ++i) {
+                    f2 qx, qy;
+                    lds128(qr + 8 * i, qx, qy);
+                    if (pending) {
+                        f2 ax, ay, bx, by;
+                        lds128(Vu + 8 * i, ax, ay);
+                        lds128(Vd + 8 * i, bx, by);
+                        const f2 vx = sub2(mul2(ax, bx), mul2(ay, by)), vy = fma2(ax, by, mul2(ay, bx));
+                        const f2 nx = sub2(mul2(qx, vx), mul2(qy, vy));
+                        qy = fma2(qx, vy, mul2(qy, vx));
+                        qx = nx;
+                        if (active) sts128(qr + 8 * i, qx, qy);
+                        const f2 qq = fma2(qx, qx, mul2(qy, qy));
+                        big = big || !(f2_lo(qq) <= 0x1p24f) || !(f2_hi(qq) <= 0x1p24f);
+                    }
+                    f2 ux, uy, dx, dy;
+                    lds128(Su + 8 * i, ux, uy);
+                    lds128(Sd + 8 * i, dx, dy);
+                    const f2 wx = sub2(fma2(ux, dx, qx), mul2(uy, dy));   // q + U
+                    const f2 wy = fma2(ux, dy, fma2(uy, dx, qy));
+                    if (i == 0) {
+                        Rx = wx; Ry = wy;
+                    } else {
+                        const f2 nx = sub2(mul2(Rx, wx), mul2(Ry, wy));
+                        Ry = fma2(Rx, wy, mul2(Ry, wx));
+                        Rx = nx;
+                    }
+                    if (big) {   // renormalise the even and the odd units' products
+                        float xl = f2_lo(Rx), yl = f2_lo(Ry), xh = f2_hi(Rx), yh = f2_hi(Ry);
+                        elo += nrm(xl, yl);
+                        ehi += nrm(xh, yh);
+                        Rx = f2_pack(xl, xh);
+                        Ry = f2_pack(yl, yh);
                     }
                 }
-                const int ex = expo<float>(prod.x, prod.y);
-                const float scl = pow2i<float>(-ex);
-                sc<float> pv{prod.x * scl, prod.y * scl, ex};
-#pragma unroll
-                for (int o = kCGL / 2; o > 0; o >>= 1) {
-                    const sc<float> w{shfl_x(pv.x, o), shfl_x(pv.y, o), __shfl_xor_sync(0xffffffffu, pv.e, o)};
-                    pv = sc_mul(pv, w);
+                float x, y;
+                int ex;
+                {
+                    float xl = f2_lo(Rx), yl = f2_lo(Ry), xh = f2_hi(Rx), yh = f2_hi(Ry);
+                    elo += nrm(xl, yl);
+                    ehi += nrm(xh, yh);
+                    x = xl * xh - yl * yh;
+                    y = xl * yh + yl * xh;
+                    ex = elo + ehi;
                 }
-                if (gl == 0 && active) gprod[tl] = pv;
+                if (SGL) {
+                    const int o2 = (MPL - 1) * 8;   // float2 index of lane 0's single unit
+                    float2 *qs = reinterpret_cast<float2 *>(qc + (size_t)tl * RF4) + o2 + gl;
+                    float qx = qs->x, qy = qs->y;
+                    if (pending) {
+                        float ax, ay, bx, by;
+                        lds64(reinterpret_cast<const float2 *>(Vu - gl) + o2 + gl, ax, ay);
+                        lds64(reinterpret_cast<const float2 *>(Vd - gl) + o2 + gl, bx, by);
+                        const float vx = ax * bx - ay * by, vy = ax * by + ay * bx;
+                        const float nx = qx * vx - qy * vy;
+                        qy = qx * vy + qy * vx;
+                        qx = nx;
+                        if (active) *qs = make_float2(qx, qy);
+                        big = big || !(qx * qx + qy * qy <= 0x1p24f);
+                    }
+                    float ux, uy, dx, dy;
+                    lds64(reinterpret_cast<const float2 *>(Su - gl) + o2 + gl, ux, uy);
+                    lds64(reinterpret_cast<const float2 *>(Sd - gl) + o2 + gl, dx, dy);
+                    const float wx = qx + ux * dx - uy * dy, wy = qy + ux * dy + uy * dx;
+                    const float nx = x * wx - y * wy;
+                    y = x * wy + y * wx;
+                    x = nx;
+                }
+                ex += nrm(x, y);
+                const unsigned bal = __ballot_sync(0xffffffffu, big);
+                const sc<float> gq = group_prod<kCGL>(sc<float>{x, y, ex});
+                if (gl == 0 && active) {
+                    if (pending) { term[tl] = nterm[tl]; tpr[tl] = ntpr[tl]; }
+                    if ((bal >> gbase) & 0xffu) bigf[tl] = 1;
+                    nterm[tl] = gq;   // prod_m (q_m + U_m) of this proposal, for the term pass
+                }
             }
             __syncthreads();
-            // ---- prefactor, new terms, and this CTA's sums of old and new terms ----
+            // ---- new terms: term x prod_m p_m x prod_m (q_m + U_m) x prefactor;
+            //      this CTA's sums of old and new terms ----
             sc<float> so{0.f, 0.f, 0}, sn{0.f, 0.f, 0};
             for (int tl = threadIdx.x; tl < ntp; tl += blockDim.x) {
                 const int t = t0 + tl;
                 const int row = md.nsign == 2 ? t >> 1 : t;
                 const int sg = t - row * md.nsign;
-                const int r = row / md.G;
-                const uint8_t *pg = prow + (size_t)(row - row0) * N;
-                const sc<float> *ESr = es + (size_t)r * 2 * N;
-                const sc<float> a = ESr[(size_t)sg * N + pg[iu]], b = ESr[(size_t)(sg ^ 1) * N + pg[id]];
-                const sc<float> gp = gprod[tl];
-                sc<float> old = term[tl];
-                if (pending) { old = nterm[tl]; term[tl] = old; }
-                // new term = old x pair product x prefactor (mantissas in [1, 2): one normalisation)
-                cx<float> m = cmul(cmul(mk(old.x, old.y), mk(gp.x, gp.y)), cmul(mk(a.x, a.y), mk(b.x, b.y)));
-                const int e = old.e + gp.e + a.e + b.e + nrm(m.x, m.y);
-                const sc<float> tn{m.x, m.y, e};
+                const int r = row / md.G, g = row - r * md.G;
+                const int ku = md.perm[(size_t)g * N + iu], kd = md.perm[(size_t)g * N + id];
+                const int rs = r * 2 * N;
+                const sc<float> a = es[rs + sg * N + ku], b = es[rs + (sg ^ 1) * N + kd];
+                const sc<float> ca = ec[rs + sg * N + ku], cb = ec[rs + (sg ^ 1) * N + kd];
+                const sc<float> gq = nterm[tl], old = term[tl];
+                const sc<float> tp = tpr[tl];
+                const cx<float> pre = cmul(mk(a.x, a.y), mk(b.x, b.y));
+                // the new term, and term x prod p after acceptance (tpr x prefactor x prod_m U_m)
+                cx<float> mn = cmul(cmul(mk(tp.x, tp.y), mk(gq.x, gq.y)), pre);
+                const int en = tp.e + gq.e + a.e + b.e + nrm(mn.x, mn.y);
+                cx<float> mp = cmul(cmul(mk(tp.x, tp.y), pre), cmul(mk(ca.x, ca.y), mk(cb.x, cb.y)));
+                const int ep = tp.e + a.e + b.e + ca.e + cb.e + nrm(mp.x, mp.y);
+                const sc<float> tn{mn.x, mn.y, en};
                 nterm[tl] = tn;
+                ntpr[tl] = sc<float>{mp.x, mp.y, ep};
                 so = sc_add(so, old);
                 sn = sc_add(sn, tn);
             }
