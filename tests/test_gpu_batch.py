@@ -118,6 +118,35 @@ def test_small_mixed_batch_matches_oracle():
         np.testing.assert_allclose(mo[i][1:4], mw[1:4], rtol=5e-5)
 
 
+def test_mixed_batch_moments_on_sampled_configurations():
+    """The batch's FP64 moments <H^n> (n = 1..4) of configurations drawn from
+    |psi|^2 by the oracle's own sampler (32 per 4x4 instance, 4 per 6x6 one:
+    the oracle's double enumeration of h2 is the cost) equal the oracle's
+    moments of its own h1, h2 to 1e-6 relative (Sec. 3.3, Eqs. 13-17)."""
+    b = nnqs.Batch(SMALL)
+    counts, spins, oms = [], [], []
+    for i, sp in enumerate(SMALL):
+        N = sp["L"] ** 2
+        p = synth.random_params(N, sp["M"], sp["K"], std=0.01, seed=900 + i)
+        b.models[i].set_params(p)
+        om = oracle.Model(sp["L"], 1.0, sp["J2"], K=sp["K"], M=sp["M"], proj_t=sp["proj_t"],
+                          proj_p=sp["proj_p"], spin_inv=sp["spin_inv"], use_bias=sp["use_bias"], params=p)
+        s, _ = om.sample(4242 + i, 4, 8, N // 2, 60) if N <= 16 else om.sample(4242 + i, 2, 2, N // 2, 60)
+        oms.append(om)
+        spins.append(s)
+        counts.append(len(s))
+    h1, h2, mo, lz = b.lanczos(_cfg(spins), counts)
+    b.status()
+    mo = mo.cpu().numpy()
+    for i, (om, s) in enumerate(zip(oms, spins)):
+        w1, w2 = om.lanczos_h(s)
+        ref = oracle.moments(w1, w2)
+        want = np.array([ref["m"][1], ref["m"][2], ref["m"][3], ref["m4"]])
+        got = np.array([mo[i][1], mo[i][2], mo[i][3], mo[i][7]])
+        assert mo[i][4] == counts[i]
+        np.testing.assert_allclose(got, want, rtol=1e-6)
+
+
 def _fits(v, M):
     gl, mpl = nnqs.nnqs_tile_shape(v)
     return gl * mpl
