@@ -8,12 +8,15 @@ K = (0,0); parameters N(0, 0.01^2) per real and imaginary part (seed 2206).
 
 One step = one pass of the hot path:
   nnqs_sample         1024 chains x 16 kept samples, n_skip = 10, n_burn = 100
-                      (266,240 Metropolis proposals, each a full psi(s')/psi(s))
+                      (266,240 Metropolis proposals, each a full psi(s')/psi(s));
+                      k_sample_cl: each chain's cache in the shared memory of a
+                      cluster of 2 CTAs
   nnqs_log_psi        fresh log psi of the 16,384 samples: the theta GEMM of
                       16,384 x 288 transformed configurations on the tcgen05
                       tensor cores (bf16 hi + lo split weights, fp32 accumulate)
   nnqs_local_energy   E_loc of the 16,384 samples (every anti-aligned J1/J2 bond
-                      -> one connected amplitude) with the FP64 sums of E_loc.
+                      -> one connected amplitude; k_eloc_fast: the per-bond
+                      tables in shared memory) with the FP64 sums of E_loc.
 Metric: projected-RBM amplitude evaluations per second (one evaluation = one
 psi(s') over all K|G| x 2 x M hidden terms: sampler proposals + fresh
 amplitudes + connected configurations of E_loc), and E_loc samples/s; the same
@@ -21,16 +24,19 @@ step in the plain FP64 GPU form is timed beside it.
 
 Beside it (the metric's second half), one p = 1 Lanczos step on the 8x8
 configuration: L = 8, M = 128, |G| = 512, no inversion, 4096 sampler-drawn
-samples; nnqs_lanczos_moments gives h1 = (H psi)/psi, h2 = (H^2 psi)/psi, the
-FP64 moments <H^n> (n <= 3) and E_p1.  Lanczos E_loc samples/s is timed on
-the full set in the FP32 engine, and on a common 512-sample subset in both
-the FP32 and the plain FP64 GPU forms for the speedup (912 = 6 x 152
-samples, whole waves of resident CTAs in both forms).  A third leg
-times fresh amplitudes of the 10x10 configuration (K = 4, M = 400, |G| = 800,
-8192 configurations), where the theta GEMM is the dominant work (512 MFLOP
-per amplitude): tcgen05 BF16X2 against the FP32 SIMT form.  A fourth leg runs
-the 64-instance mixed batch (one autotune, then one replay of the persistent
-graph-captured launch = one Lanczos step of every instance).
+samples; nnqs_lanczos_partial gives h1 = (H psi)/psi, h2 = (H^2 psi)/psi
+(k_lanczos_fast) and the raw FP64 sums, which are all-reduced over the ranks
+before nnqs_lanczos_finish forms <H^n> (n <= 3) and E_p1.  Lanczos E_loc
+samples/s is timed on the full set, and on a common 912-sample subset in both
+the FP32 and the plain FP64 GPU forms for the speedup (912 = 6 x 152 samples,
+whole waves of resident CTAs in both forms).  A third leg times fresh
+amplitudes of the 10x10 configuration (K = 4, M = 400, |G| = 800, 8192
+configurations), where the theta GEMM is the dominant work (512 MFLOP per
+amplitude): tcgen05 BF16X2 against the FP32 SIMT form.  A fourth leg runs the
+64-instance mixed batch (one autotune, then one replay of the persistent
+graph-captured launch = one Lanczos step of every instance).  A fifth leg runs
+one stochastic-reconfiguration step of the 10x10 configuration (sampling, log
+psi, E_loc, O_k, F and the CG solve on the device).
 
 Timing: CUDA events on the launching stream, per step, with a 512 MB L2 flush
 before every timed step (outside the events); W warm-up steps; barrier and the
@@ -682,7 +688,7 @@ def main():
                    "precision": "BF16X2 theta GEMM on tensor cores for fresh amplitudes; FP32 with exact exponent tracking elsewhere", "l2": "flushed (512 MB write) before every step"},
         "eloc_samples_per_s": world * N_SAMPLES / (ms / 1e3),
         "acceptance": res["acc"], "E_loc_mean_per_site": res["e_mean"],
-        "roofline": {"kernel": "k_eloc (E_loc connected-amplitude engine)", "bound": "alu",
+        "roofline": {"kernel": "k_eloc_fast (E_loc with the per-bond tables in shared memory)", "bound": "alu",
                      "achieved": eloc_ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": eloc_ach / FP32_PEAK_TFLOPS, "traffic": K_RATIO_TRAFFIC,
                      "peak_source": f"FP32 FMA, {ALU_SOURCE}",
