@@ -246,16 +246,18 @@ int nnqs_grad_logpsi(nnqs_model *model, const uint64_t *cfg, int64_t n, double *
 /* Energy gradient F_k = <conj(O_k) (E_loc - <E_loc>)> over n samples (the
  * right-hand side of Eq. 12 without -dtau); for real coordinates
  * dE/dRe alpha_k = 2 Re F_k and dE/dIm alpha_k = 2 Im F_k.
- * O: [n][P][2], eloc: [n][2], F_out: [P][2] (all device, FP64).  weights:
- * [n] device doubles, or NULL for plain means over samples drawn from |psi|^2
- * (with weights |psi|^2 over a complete basis the result is the exact
- * gradient). */
+ * O: [n][P][2], eloc: [n][2], F_out: [P][2] (all device, FP64; O 16-byte
+ * aligned, else NNQS_EINVAL).  weights: [n] device doubles, or NULL for plain
+ * means over samples drawn from |psi|^2 (with weights |psi|^2 over a complete
+ * basis the result is the exact gradient).  Uses the model's workspace
+ * (2 P doubles per chunk of samples, at most 128 chunks). */
 int nnqs_energy_grad(const nnqs_model *model, const double *O, const double *eloc, const double *weights, int64_t n,
                      double *F_out, void *stream);
 
 /* Matrix-free SR product (Eq. 12): y = (S + lambda I) x with
  * S_kk' = <conj(O_k) O_k'> - <conj(O_k)><O_k'>, accumulated in FP64.
- * O: [n][P][2], x, y: [P][2] (device); weights as for nnqs_energy_grad. */
+ * O: [n][P][2], x, y: [P][2] (device; O and x 16-byte aligned, else
+ * NNQS_EINVAL); weights as for nnqs_energy_grad. */
 int nnqs_sr_matvec(const nnqs_model *model, const double *O, const double *weights, int64_t n, const double *x,
                    double lambda, double *y, void *stream);
 
@@ -263,7 +265,8 @@ int nnqs_sr_matvec(const nnqs_model *model, const double *O, const double *weigh
  * solves (S + lambda I) delta = -dtau F by conjugate gradients in FP64,
  * matrix-free, entirely on the device (no host synchronisation; at most
  * max_iter iterations, stopping once |r| <= tol |dtau F|).
- * O: [n][P][2], F: [P][2], delta_out: [P][2] (device).
+ * O: [n][P][2] (16-byte aligned, else NNQS_EINVAL), F: [P][2], delta_out: [P][2]
+ * (device).
  * info_out (device [2] doubles, may be NULL): {iterations, |r| / |b|}.
  * params_inout (device [P][2], may be NULL): if given, delta is added to it
  * (the parameter update alpha += delta; follow with nnqs_set_params_device). */

@@ -636,9 +636,27 @@ int nnqs_grad_logpsi(nnqs_model *m, const uint64_t *cfg, int64_t n, double *O, v
         } else {
             const DevModel<float> v = view<float>(m);
             const int grid = grad_grid(v, n, m->nsm);
-            int rc = ensure_ws(m, grad_scratch_bytes(v) * grid);
+            const size_t gs = align256(grad_scratch_bytes(v) * grid);
+            // tensor-core models: theta' of a chunk of samples from the tcgen05
+            // GEMM (at most 4 GiB of [K][G][M] float2 rows at a time), then the
+            // gradient kernel reads it
+            const size_t per = (size_t)v.K * v.G * v.M * sizeof(float2);
+            int64_t cs = 0;
+            if (m->ns) cs = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(((size_t)4 << 30) / per)));
+            int rc = ensure_ws(m, gs + (size_t)cs * per);
             if (rc) return rc;
-            e = launch_grad(v, cfg, n, O, m->ws, grid, st);
+            if (!cs) {
+                e = launch_grad(v, cfg, n, O, m->ws, grid, st);
+            } else {
+                float2 *th = reinterpret_cast<float2 *>((char *)m->ws + gs);
+                e = cudaSuccess;
+                for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += cs) {
+                    const int64_t k = std::min<int64_t>(cs, n - c0);
+                    const uint64_t *c = cfg + c0 * m->nwords;
+                    e = launch_log_psi_tc(v, m->bimg, m->pinv, m->ns, c, k, nullptr, m->nsm, st, th);
+                    if (e == cudaSuccess) e = launch_grad(v, c, k, O + c0 * m->P * 2, m->ws, grad_grid(v, k, m->nsm), st, th);
+                }
+            }
         }
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "grad_logpsi");
     });
@@ -651,8 +669,9 @@ int nnqs_energy_grad(const nnqs_model *mc, const double *O, const double *eloc, 
     if (check_model(m)) return NNQS_EINVAL;
     if (n <= 0) return fail(NNQS_EINVAL, "n must be > 0");
     if (!O || !eloc || !F) return fail(NNQS_EINVAL, "O, eloc and F_out must be non-NULL");
+    if ((uintptr_t)O & 15) return fail(NNQS_EINVAL, "O must be 16-byte aligned");
     return with_device(m, [&]() -> int {
-        int rc = ensure_ws(m, 256 * sizeof(double));
+        int rc = ensure_ws(m, egrad_scratch_doubles(n, m->P) * sizeof(double));
         if (rc) return rc;
         cudaError_t e = launch_energy_grad(O, eloc, weights, n, m->P, F, (double *)m->ws, (cudaStream_t)stream);
         return e == cudaSuccess ? NNQS_OK : cuda_fail(e, "energy_grad");
@@ -666,6 +685,7 @@ int nnqs_sr_matvec(const nnqs_model *mc, const double *O, const double *weights,
     if (check_model(m)) return NNQS_EINVAL;
     if (n <= 0) return fail(NNQS_EINVAL, "n must be > 0");
     if (!O || !x || !y) return fail(NNQS_EINVAL, "O, x and y must be non-NULL");
+    if (((uintptr_t)O | (uintptr_t)x) & 15) return fail(NNQS_EINVAL, "O and x must be 16-byte aligned");
     return with_device(m, [&]() -> int {
         int rc = ensure_ws(m, sr_scratch_doubles(n, m->P) * sizeof(double));
         if (rc) return rc;
@@ -684,6 +704,7 @@ int nnqs_sr_solve(const nnqs_model *mc, const double *O, const double *weights, 
     if (max_iter < 0 || max_iter > 100000) return fail(NNQS_EINVAL, "max_iter must be in 0..100000");
     if (!(lambda >= 0) || !(tol >= 0)) return fail(NNQS_EINVAL, "lambda and tol must be >= 0");
     if (!O || !F || !delta) return fail(NNQS_EINVAL, "O, F and delta_out must be non-NULL");
+    if ((uintptr_t)O & 15) return fail(NNQS_EINVAL, "O must be 16-byte aligned");
     return with_device(m, [&]() -> int {
         int rc = ensure_ws(m, sr_scratch_doubles(n, m->P) * sizeof(double));
         if (rc) return rc;

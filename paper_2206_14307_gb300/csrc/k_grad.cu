@@ -25,7 +25,7 @@ template <typename T> size_t grad_scratch_bytes(const DevModel<T> &md)
 template <typename T, int MPL>
 __global__ void __launch_bounds__(kThreads) k_grad(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
                                                    double *__restrict__ O, unsigned char *__restrict__ scratch,
-                                                   size_t scratch_stride)
+                                                   size_t scratch_stride, const float2 *__restrict__ th)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int8_t *tg = reinterpret_cast<int8_t *>(smem_raw);  // [G][N]  (T_g s)_k
@@ -64,13 +64,23 @@ __global__ void __launch_bounds__(kThreads) k_grad(DevModel<T> md, const uint64_
                 cx<T> thp[MPL];
 #pragma unroll
                 for (int j = 0; j < MPL; ++j) thp[j] = cx<T>{T(0), T(0)};
-                for (int i = 0; i < N; ++i) {
-                    const cx<T> *wk = Wr + (size_t)pg[i] * M;
-                    const T si = s_sm[i];
+                if (th) {
+                    // theta' of the row from the tensor cores
+                    const float2 *tr = th + ((smp * K + r) * (int64_t)G + g) * M;
 #pragma unroll
                     for (int j = 0; j < MPL; ++j) {
                         const int m = lane + 32 * j;
-                        if (m < M) { const cx<T> ww = wk[m]; thp[j].x += si * ww.x; thp[j].y += si * ww.y; }
+                        if (m < M) { const float2 v = tr[m]; thp[j] = cx<T>{T(v.x), T(v.y)}; }
+                    }
+                } else {
+                    for (int i = 0; i < N; ++i) {
+                        const cx<T> *wk = Wr + (size_t)pg[i] * M;
+                        const T si = s_sm[i];
+#pragma unroll
+                        for (int j = 0; j < MPL; ++j) {
+                            const int m = lane + 32 * j;
+                            if (m < M) { const cx<T> ww = wk[m]; thp[j].x += si * ww.x; thp[j].y += si * ww.y; }
+                        }
                     }
                 }
                 cx<T> at{T(0), T(0)};
@@ -208,7 +218,7 @@ template <typename T> int grad_grid(const DevModel<T> &md, int64_t n, int nsm)
 
 template <typename T>
 cudaError_t launch_grad(const DevModel<T> &md, const uint64_t *cfg, int64_t n, double *O, void *scratch, int grid,
-                        cudaStream_t st)
+                        cudaStream_t st, const float2 *th)
 {
     if (n <= 0) return cudaSuccess;
     const int g = grid;
@@ -219,7 +229,7 @@ cudaError_t launch_grad(const DevModel<T> &md, const uint64_t *cfg, int64_t n, d
 #define NNQS_CASE(V)                                                                                              \
     case V:                                                                                                       \
         err = cudaFuncSetAttribute(k_grad<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
-        if (err == cudaSuccess) k_grad<T, V><<<g, kThreads, smem, st>>>(md, cfg, n, O, (unsigned char *)scratch, stride); \
+        if (err == cudaSuccess) k_grad<T, V><<<g, kThreads, smem, st>>>(md, cfg, n, O, (unsigned char *)scratch, stride, th); \
         break;
         NNQS_CASE(1) NNQS_CASE(2) NNQS_CASE(3) NNQS_CASE(4) NNQS_CASE(6) NNQS_CASE(8) NNQS_CASE(13) NNQS_CASE(16)
 #undef NNQS_CASE
@@ -232,7 +242,7 @@ template int grad_grid<float>(const DevModel<float> &, int64_t, int);
 template int grad_grid<double>(const DevModel<double> &, int64_t, int);
 template size_t grad_scratch_bytes<float>(const DevModel<float> &);
 template size_t grad_scratch_bytes<double>(const DevModel<double> &);
-template cudaError_t launch_grad<float>(const DevModel<float> &, const uint64_t *, int64_t, double *, void *, int, cudaStream_t);
-template cudaError_t launch_grad<double>(const DevModel<double> &, const uint64_t *, int64_t, double *, void *, int, cudaStream_t);
+template cudaError_t launch_grad<float>(const DevModel<float> &, const uint64_t *, int64_t, double *, void *, int, cudaStream_t, const float2 *);
+template cudaError_t launch_grad<double>(const DevModel<double> &, const uint64_t *, int64_t, double *, void *, int, cudaStream_t, const float2 *);
 
 }  // namespace nnqs

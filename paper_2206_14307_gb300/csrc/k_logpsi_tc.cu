@@ -188,7 +188,8 @@ static cudaError_t launch_by_mq(int mq, const DevModel<float> &md, const TcArgs 
 }
 
 cudaError_t launch_log_psi_tc(const DevModel<float> &md, const uint16_t *bimg, const uint16_t *pinv, int NS,
-                              const uint64_t *cfg, int64_t n, double *out, int nsm, cudaStream_t st)
+                              const uint64_t *cfg, int64_t n, double *out, int nsm, cudaStream_t st,
+                              float2 *theta_out)
 {
     if (n <= 0) return cudaSuccess;
     TcArgs ta;
@@ -196,6 +197,7 @@ cudaError_t launch_log_psi_tc(const DevModel<float> &md, const uint16_t *bimg, c
     if (!ta.p.ok) return cudaErrorInvalidValue;
     ta.bimg = bimg;
     ta.pinv = pinv;
+    ta.theta_out = theta_out;
     ta.skip_first_copy = test_hook_enabled("NNQS_TEST_SKIP_TC_COPY");
     const int64_t nsuper = (n + ta.p.S - 1) / ta.p.S;
     const int grid = (int)(nsuper < nsm ? nsuper : nsm);

@@ -279,7 +279,25 @@ struct TcArgs {
     const uint16_t *pinv;     // [G][KD1]: (T_g s)_j = s_{pinv[g][j]}; N marks padding
     int skip_first_copy;      // test hook: arm the first image barrier but issue no copy, so
                               // its bounded wait runs out (NNQS_ETIMEOUT) with nothing in flight
+    float2 *theta_out;        // non-NULL: write theta' = W.t [n][K][G][M] instead of log psi
 };
+
+// theta' = W.t of this thread's row and MT/4 units of the accumulator at tb
+// (no bias), to th[m0 .. m0 + MT/4) within the tile's units
+__device__ __forceinline__ void theta_store(uint32_t tb, int MT, int m0, int mbase, int M, float2 *th)
+{
+    for (int c = 0; c < MT / 4; c += 2) {
+        float r0, r1, i0, i1;
+        tc::tmem_ld2(tb + (uint32_t)(m0 + c), r0, r1);
+        tc::tmem_ld2(tb + (uint32_t)(MT + m0 + c), i0, i1);
+        tc::tmem_wait_ld();
+        const int m = mbase + m0 + c;
+        if (th) {
+            if (m < M) th[m] = make_float2(r0, i0);
+            if (m + 1 < M) th[m + 1] = make_float2(r1, i1);
+        }
+    }
+}
 
 struct Blk {
     int64_t st;
@@ -526,14 +544,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (ready) {
                 const int m0 = cg * (MT / 4);
                 const uint32_t tb = taddr + (uint32_t)ai * 256u + ((uint32_t)(quad * 32) << 16);
-                const float4 *slice = reinterpret_cast<const float4 *>(
-                    P.resident ? img_smem(cur, ai) + tc_slice_off(P) : smem + P.off_sl + (uint32_t)(j % 3) * P.slice_bytes);
-                epi_block<MQ, NSIGN>(tb, MT, m0, slice + m0, slice[MT], pp, pm);
+                if (ta.theta_out) {
+                    const int qg = cur.t * 128 + quad * 32 + lane;
+                    const int sl = qg / G, g = qg - sl * G;
+                    const int64_t s = cur.st * P.S + sl;
+                    float2 *th = s < n ? ta.theta_out + ((s * P.K + cur.r) * (int64_t)G + g) * P.M : nullptr;
+                    theta_store(tb, MT, m0, cur.mt * MT, P.M, th);
+                } else {
+                    const float4 *slice = reinterpret_cast<const float4 *>(
+                        P.resident ? img_smem(cur, ai) + tc_slice_off(P) : smem + P.off_sl + (uint32_t)(j % 3) * P.slice_bytes);
+                    epi_block<MQ, NSIGN>(tb, MT, m0, slice + m0, slice[MT], pp, pm);
+                }
             }
             tc::fence_before_sync();
 
             // ---- after the last hidden tile of (tile, r): row terms -> per-sample sums ----
-            if (cur.mt == P.nmt - 1) {
+            if (cur.mt == P.nmt - 1 && !ta.theta_out) {
                 const int row = quad * 32 + lane;
                 if (cg > 0) {
                     float *xb = xbuf + ((cg - 1) * 128 + row) * 6;

@@ -14,7 +14,8 @@ namespace nnqs {
 
 constexpr int kSrThreads = 256;
 constexpr int kDotBlocks = 128;
-constexpr int kSrChunksMax = 128;   // sample chunks of the two-pass S x product
+constexpr int kSrChunksMax = 128;   // sample chunks of the two-pass S x product and of F
+constexpr int kOvSplit = 16;        // blocks per sample of the O x product
 
 // scratch layout (doubles)
 //   [0, 16)          CG state: 0 rr, 1 pAp, 2 alpha, 3 beta, 4 |b|^2, 5 done, 6 iterations, 7 W, 8-9 mean
@@ -26,8 +27,10 @@ constexpr int kStateDoubles = 16;
 size_t sr_scratch_doubles(int64_t n, int64_t P)
 {
     // state, dot partials, z [n][2], r, p, Ap [P][2], the matvec's state block,
-    // and the chunk partials [kSrChunks][P][4] of the S x product
-    return kStateDoubles + 2 * kDotBlocks + 2 * (size_t)n + 6 * (size_t)P + 64 + (size_t)kSrChunksMax * 4 * (size_t)P;
+    // the chunk partials [kSrChunks][P][2] of the S x product, the split
+    // partials [n][kOvSplit][2] of O x and zeta [n][2]
+    return kStateDoubles + 2 * kDotBlocks + 2 * (size_t)n + 6 * (size_t)P + 64 + (size_t)kSrChunksMax * 2 * (size_t)P +
+           2 * (size_t)kOvSplit * (size_t)n + 2 * (size_t)n;
 }
 
 template <int NV>
@@ -70,107 +73,186 @@ __global__ void __launch_bounds__(kSrThreads) k_wmean(const double *__restrict__
     }
 }
 
-// F_k = (1/W) sum_s w_s conj(O_sk) (e_s - ebar)
-__global__ void k_energy_grad(const double *__restrict__ O, const double *__restrict__ e, const double *__restrict__ w,
-                              const double *__restrict__ state, int64_t n, int64_t P, double *__restrict__ F)
-{
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= P) return;
-    const double bx = state[S_MEAN], by = state[S_MEAN + 1], W = state[S_W];
-    double fx = 0, fy = 0;
-    for (int64_t s = 0; s < n; ++s) {
-        const double ws = w ? w[s] : 1.0;
-        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
-        const double dx = e[2 * s] - bx, dy = e[2 * s + 1] - by;
-        fx += ws * (ox * dx + oy * dy);
-        fy += ws * (ox * dy - oy * dx);
-    }
-    F[2 * k] = fx / W;
-    F[2 * k + 1] = fy / W;
-}
-
-cudaError_t launch_energy_grad(const double *O, const double *eloc, const double *w, int64_t n, int64_t P, double *F,
-                               double *scratch, cudaStream_t st)
-{
-    k_wmean<<<1, kSrThreads, 0, st>>>(eloc, w, n, scratch);
-    k_energy_grad<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(O, eloc, w, scratch, n, P, F);
-    return cudaGetLastError();
-}
-
-// z_s = sum_k O_sk x_k  (one block per sample); skipped once the solve converged
-__global__ void __launch_bounds__(kSrThreads) k_ov(const double *__restrict__ O, const double *__restrict__ x, int64_t P,
-                                                   double *__restrict__ z, const double *__restrict__ state)
-{
-    if (state && state[S_DONE] != 0.0) return;
-    __shared__ double sh[kSrThreads / 32][2];
-    const int64_t s = blockIdx.x;
-    double a[2] = {0, 0};
-    for (int64_t k = threadIdx.x; k < P; k += blockDim.x) {
-        const double ox = O[(s * P + k) * 2], oy = O[(s * P + k) * 2 + 1];
-        const double xx = x[2 * k], xy = x[2 * k + 1];
-        a[0] += ox * xx - oy * xy;
-        a[1] += ox * xy + oy * xx;
-    }
-    blk_sum<2>(a, sh);
-    if (threadIdx.x == 0) { z[2 * s] = a[0]; z[2 * s + 1] = a[1]; }
-}
-
-// y_k = (1/W) sum_s w_s conj(O_sk) z_s - conj(Obar_k) zbar + lambda x_k, in two
-// passes over sample chunks: pass 1 (block (k tile, chunk c)) sums samples of
-// chunk c for 256 consecutive k -- coalesced rows of O -- into part[c][k];
-// pass 2 adds the chunks in order (deterministic) and forms y.
-constexpr int kSrChunks = kSrChunksMax;
-__global__ void __launch_bounds__(256) k_sr_part(const double *__restrict__ O, const double *__restrict__ z,
-                                                 const double *__restrict__ w, int64_t n, int64_t P, int64_t chunk,
-                                                 double *__restrict__ part, const double *__restrict__ state)
+// Both F and S x are sums over samples of conj(O_sk) zeta_s with a per-sample
+// coefficient zeta (F: w_s (e_s - ebar)/W; S x: w_s (z_s - zbar)/W, which
+// folds the <conj O><O x> term in), i.e. 4 FP64 FMAs per complex element of O
+// -- on GB300 (FP64 at 1/74 of FP32) that, not HBM, bounds a pass over O.
+// Two passes over sample chunks: pass 1 (block (k tile, chunk c)) reads rows
+// of O coalesced (16 B per k) into part[c][k], pass 2 adds the chunks in order
+// (deterministic) and adds lambda x.
+__global__ void __launch_bounds__(256) k_oz_part(const double *__restrict__ O, const double *__restrict__ zeta,
+                                                 int64_t n, int64_t P, int64_t chunk, double *__restrict__ part,
+                                                 const double *__restrict__ state)
 {
     if (state && state[S_DONE] != 0.0) return;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= P) return;
     const int64_t s0 = blockIdx.y * chunk, s1 = s0 + chunk < n ? s0 + chunk : n;
-    double ax = 0, ay = 0, mx = 0, my = 0;
-#pragma unroll 4
-    for (int64_t s = s0; s < s1; ++s) {
-        const double ws = w ? w[s] : 1.0;
-        const double2 o = *reinterpret_cast<const double2 *>(O + (s * P + k) * 2);
-        const double zx = z[2 * s], zy = z[2 * s + 1];
-        ax += ws * (o.x * zx + o.y * zy);
-        ay += ws * (o.x * zy - o.y * zx);
-        mx += ws * o.x;
-        my += ws * o.y;
+    double ax = 0, ay = 0, bx = 0, by = 0;
+    int64_t s = s0;
+    for (; s + 1 < s1; s += 2) {
+        const double2 o0 = *reinterpret_cast<const double2 *>(O + (s * P + k) * 2);
+        const double2 o1 = *reinterpret_cast<const double2 *>(O + ((s + 1) * P + k) * 2);
+        const double2 z0 = *reinterpret_cast<const double2 *>(zeta + 2 * s);
+        const double2 z1 = *reinterpret_cast<const double2 *>(zeta + 2 * s + 2);
+        ax = fma(o0.x, z0.x, fma(o0.y, z0.y, ax));
+        ay = fma(o0.x, z0.y, fma(-o0.y, z0.x, ay));
+        bx = fma(o1.x, z1.x, fma(o1.y, z1.y, bx));
+        by = fma(o1.x, z1.y, fma(-o1.y, z1.x, by));
     }
-    double *pp = part + ((int64_t)blockIdx.y * P + k) * 4;
-    pp[0] = ax; pp[1] = ay; pp[2] = mx; pp[3] = my;
+    if (s < s1) {
+        const double2 o0 = *reinterpret_cast<const double2 *>(O + (s * P + k) * 2);
+        const double2 z0 = *reinterpret_cast<const double2 *>(zeta + 2 * s);
+        ax = fma(o0.x, z0.x, fma(o0.y, z0.y, ax));
+        ay = fma(o0.x, z0.y, fma(-o0.y, z0.x, ay));
+    }
+    double *pp = part + ((int64_t)blockIdx.y * P + k) * 2;
+    pp[0] = ax + bx;
+    pp[1] = ay + by;
 }
 
-__global__ void k_sr_out(const double *__restrict__ part, int nch, const double *__restrict__ zst,
-                         const double *__restrict__ x, double lambda, int64_t P, double *__restrict__ y,
-                         const double *__restrict__ state)
+// y_k = sum_c part[c][k] (+ lambda x_k when x is given)
+__global__ void k_oz_out(const double *__restrict__ part, int nch, const double *__restrict__ x, double lambda,
+                         int64_t P, double *__restrict__ y, const double *__restrict__ state)
 {
     if (state && state[S_DONE] != 0.0) return;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= P) return;
-    double ax = 0, ay = 0, mx = 0, my = 0;
+    double ax = 0, ay = 0;
     for (int c = 0; c < nch; ++c) {
-        const double *pp = part + ((int64_t)c * P + k) * 4;
-        ax += pp[0]; ay += pp[1]; mx += pp[2]; my += pp[3];
+        ax += part[((int64_t)c * P + k) * 2];
+        ay += part[((int64_t)c * P + k) * 2 + 1];
     }
-    const double inv = 1.0 / zst[S_W];
-    ax *= inv; ay *= inv; mx *= inv; my *= inv;
-    const double bx = zst[S_MEAN], by = zst[S_MEAN + 1];
-    y[2 * k] = ax - (mx * bx + my * by) + lambda * x[2 * k];
-    y[2 * k + 1] = ay - (mx * by - my * bx) + lambda * x[2 * k + 1];
+    if (x) {
+        ax += lambda * x[2 * k];
+        ay += lambda * x[2 * k + 1];
+    }
+    y[2 * k] = ax;
+    y[2 * k + 1] = ay;
 }
 
+// zeta_s = w_s (v_s - vbar) / W from a state block holding vbar and W
+__global__ void k_zeta(const double *__restrict__ v, const double *__restrict__ w, int64_t n,
+                       const double *__restrict__ vst, double *__restrict__ zeta, const double *__restrict__ state)
+{
+    if (state && state[S_DONE] != 0.0) return;
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double f = (w ? w[s] : 1.0) / vst[S_W];
+    zeta[2 * s] = f * (v[2 * s] - vst[S_MEAN]);
+    zeta[2 * s + 1] = f * (v[2 * s + 1] - vst[S_MEAN + 1]);
+}
+
+static int sr_nch(int64_t n, int64_t &chunk)
+{
+    chunk = (n + kSrChunksMax - 1) / kSrChunksMax;
+    return (int)((n + chunk - 1) / chunk);
+}
+
+size_t egrad_scratch_doubles(int64_t n, int64_t P)
+{
+    int64_t chunk;
+    const int nch = sr_nch(n, chunk);
+    return kStateDoubles + 2 * (size_t)n + 2 * (size_t)nch * (size_t)P;
+}
+
+// F_k = (1/W) sum_s w_s conj(O_sk) (e_s - ebar)
+cudaError_t launch_energy_grad(const double *O, const double *eloc, const double *w, int64_t n, int64_t P, double *F,
+                               double *scratch, cudaStream_t st)
+{
+    int64_t chunk;
+    const int nch = sr_nch(n, chunk);
+    double *zeta = scratch + kStateDoubles;
+    double *part = zeta + 2 * n;
+    k_wmean<<<1, kSrThreads, 0, st>>>(eloc, w, n, scratch);
+    k_zeta<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(eloc, w, n, scratch, zeta, nullptr);
+    k_oz_part<<<dim3((unsigned)((P + 255) / 256), (unsigned)nch), 256, 0, st>>>(O, zeta, n, P, chunk, part, nullptr);
+    k_oz_out<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(part, nch, nullptr, 0.0, P, F, nullptr);
+    return cudaGetLastError();
+}
+
+// z_s = sum_k O_sk x_k: kOvSplit blocks per sample, each a contiguous slice of
+// the row with two 16-byte loads in flight per thread; the partial sums go to
+// zpart [n][kOvSplit] (added in order by k_zsum).  Skipped once the solve
+// converged.
+__global__ void __launch_bounds__(kSrThreads) k_ov(const double *__restrict__ O, const double *__restrict__ x, int64_t P,
+                                                   double *__restrict__ zpart, const double *__restrict__ state)
+{
+    if (state && state[S_DONE] != 0.0) return;
+    __shared__ double sh[kSrThreads / 32][2];
+    const int64_t s = blockIdx.x / kOvSplit;
+    const int sp = blockIdx.x % kOvSplit;
+    const int64_t len = (P + kOvSplit - 1) / kOvSplit;
+    const int64_t k0 = sp * len, k1 = k0 + len < P ? k0 + len : P;
+    const double2 *Os = reinterpret_cast<const double2 *>(O) + s * P;
+    const double2 *xv = reinterpret_cast<const double2 *>(x);
+    double a[2] = {0, 0}, b0 = 0, b1 = 0;
+    int64_t k = k0 + threadIdx.x;
+    for (; k + kSrThreads < k1; k += 2 * kSrThreads) {
+        const double2 o0 = Os[k], o1 = Os[k + kSrThreads];
+        const double2 x0 = xv[k], x1 = xv[k + kSrThreads];
+        a[0] += o0.x * x0.x - o0.y * x0.y;
+        a[1] += o0.x * x0.y + o0.y * x0.x;
+        b0 += o1.x * x1.x - o1.y * x1.y;
+        b1 += o1.x * x1.y + o1.y * x1.x;
+    }
+    if (k < k1) {
+        const double2 o0 = Os[k], x0 = xv[k];
+        a[0] += o0.x * x0.x - o0.y * x0.y;
+        a[1] += o0.x * x0.y + o0.y * x0.x;
+    }
+    a[0] += b0;
+    a[1] += b1;
+    blk_sum<2>(a, sh);
+    if (threadIdx.x == 0) {
+        zpart[(s * kOvSplit + sp) * 2] = a[0];
+        zpart[(s * kOvSplit + sp) * 2 + 1] = a[1];
+    }
+}
+
+// z_s from its split partials (in order), and the weighted mean of z (one block)
+__global__ void __launch_bounds__(kSrThreads) k_zsum(const double *__restrict__ zpart, const double *__restrict__ w,
+                                                     int64_t n, double *__restrict__ z, double *__restrict__ zst,
+                                                     const double *__restrict__ state)
+{
+    if (state && state[S_DONE] != 0.0) return;
+    __shared__ double sh[kSrThreads / 32][3];
+    double a[3] = {0, 0, 0};
+    for (int64_t s = threadIdx.x; s < n; s += blockDim.x) {
+        double zx = 0, zy = 0;
+        for (int q = 0; q < kOvSplit; ++q) {
+            zx += zpart[(s * kOvSplit + q) * 2];
+            zy += zpart[(s * kOvSplit + q) * 2 + 1];
+        }
+        z[2 * s] = zx;
+        z[2 * s + 1] = zy;
+        const double ws = w ? w[s] : 1.0;
+        a[0] += ws * zx;
+        a[1] += ws * zy;
+        a[2] += ws;
+    }
+    blk_sum<3>(a, sh);
+    if (threadIdx.x == 0) {
+        zst[S_MEAN] = a[0] / a[2];
+        zst[S_MEAN + 1] = a[1] / a[2];
+        zst[S_W] = a[2];
+    }
+}
+
+// (S + lambda) x: z = O x (k_ov, k_zsum: z and its weighted mean), zeta,
+// then y = sum_s conj(O_s) zeta_s + lambda x
 static void matvec(const double *O, const double *w, int64_t n, int64_t P, const double *x, double lambda, double *y,
                    double *z, double *zst, double *part, const double *state, cudaStream_t st)
 {
-    const int64_t chunk = (n + kSrChunks - 1) / kSrChunks;
-    const int nch = (int)((n + chunk - 1) / chunk);
-    k_ov<<<(unsigned)n, kSrThreads, 0, st>>>(O, x, P, z, state);
-    k_wmean<<<1, kSrThreads, 0, st>>>(z, w, n, zst);
-    k_sr_part<<<dim3((unsigned)((P + 255) / 256), (unsigned)nch), 256, 0, st>>>(O, z, w, n, P, chunk, part, state);
-    k_sr_out<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(part, nch, zst, x, lambda, P, y, state);
+    int64_t chunk;
+    const int nch = sr_nch(n, chunk);
+    double *zpart = part + (size_t)kSrChunksMax * 2 * (size_t)P;
+    double *zeta = zpart + 2 * (size_t)kOvSplit * (size_t)n;
+    k_ov<<<(unsigned)(n * kOvSplit), kSrThreads, 0, st>>>(O, x, P, zpart, state);
+    k_zsum<<<1, kSrThreads, 0, st>>>(zpart, w, n, z, zst, state);
+    k_zeta<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(z, w, n, zst, zeta, state);
+    k_oz_part<<<dim3((unsigned)((P + 255) / 256), (unsigned)nch), 256, 0, st>>>(O, zeta, n, P, chunk, part, state);
+    k_oz_out<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(part, nch, x, lambda, P, y, state);
 }
 
 cudaError_t launch_sr_matvec(const double *O, const double *w, int64_t n, int64_t P, const double *x, double lambda,

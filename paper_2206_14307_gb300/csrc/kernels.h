@@ -84,9 +84,12 @@ bool launch_sample_cl(const DevModel<float> &md, uint64_t seed, int n_chains, in
 template <typename T> size_t grad_scratch_bytes(const DevModel<T> &md);
 template <typename T> int grad_grid(const DevModel<T> &md, int64_t n, int nsm);
 
+// th (FP32 only, may be NULL): theta' = W.(T_g s) of every row of the n
+// configurations, [n][K][G][M] (launch_log_psi_tc's theta output), read
+// instead of computed
 template <typename T>
 cudaError_t launch_grad(const DevModel<T> &md, const uint64_t *cfg, int64_t n, double *O, void *scratch, int grid,
-                        cudaStream_t st);
+                        cudaStream_t st, const float2 *th = nullptr);
 
 // configurations annihilated by the projection: mode 0 sets log psi = -inf,
 // mode 1 sets h1/h2 (either may be NULL) to NaN and flags NNQS_ERANGE
@@ -131,6 +134,7 @@ cudaError_t launch_eloc_sums(const double *eloc, int64_t n, double *partial, int
                              cudaStream_t st);
 // SR pieces (Eq. 12), all in FP64; weights may be NULL (plain sample means)
 size_t sr_scratch_doubles(int64_t n, int64_t P);
+size_t egrad_scratch_doubles(int64_t n, int64_t P);
 cudaError_t launch_energy_grad(const double *O, const double *eloc, const double *w, int64_t n, int64_t P, double *F,
                                double *scratch, cudaStream_t st);
 cudaError_t launch_sr_matvec(const double *O, const double *w, int64_t n, int64_t P, const double *x, double lambda,
@@ -158,7 +162,10 @@ size_t tc_pinv_bytes(int N, int G);
 void tc_pinv_table(const uint8_t *perm, int N, int G, uint16_t *out);
 cudaError_t launch_bimg(const double *params, int N, int M, int G, int K, int nsign, int NS, int use_bias,
                         uint16_t *img, cudaStream_t st);
+// theta_out non-NULL: writes theta' = W.(T_g s) (no bias) of every row,
+// [n][K][G][M] float2, instead of log psi (out unused)
 cudaError_t launch_log_psi_tc(const DevModel<float> &md, const uint16_t *bimg, const uint16_t *pinv, int NS,
-                              const uint64_t *cfg, int64_t n, double *out, int nsm, cudaStream_t st);
+                              const uint64_t *cfg, int64_t n, double *out, int nsm, cudaStream_t st,
+                              float2 *theta_out = nullptr);
 
 }  // namespace nnqs

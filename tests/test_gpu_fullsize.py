@@ -60,6 +60,12 @@ def test_10x10_K4_full_batch_sampled_outputs():
     Ow = om.grad_logpsi(s[idx])
     assert O.shape == (len(idx), K * (1 + N + M + M * N))
     assert np.max(np.abs(O - Ow)) <= 1e-5 * max(1.0, np.abs(Ow).max())
+    # the tensor-core form (theta' of the rows from the tcgen05 GEMM)
+    bm = nnqs.Model(L, 1.0, 0.5, K=K, M=M, proj_t=True, proj_p=True, spin_inv=0, precision=nnqs.BF16X2)
+    bm.set_params(p)
+    Ob = to_complex(bm.grad_logpsi(sub))
+    bm.status()
+    assert np.max(np.abs(Ob - Ow)) <= 1e-5 * max(1.0, np.abs(Ow).max())
 
 
 def test_8x8_lanczos_step_full_batch():

@@ -15,7 +15,7 @@ from tests.helpers import annihilated, assert_logpsi_close, fp32_rtol, make_pair
 
 pytestmark = pytest.mark.gpu
 
-FP64, FP32 = 0, 1
+FP64, FP32, BF16X2, BF16X3 = 0, 1, 2, 3
 TOL = {FP64: 1e-9, FP32: 1e-5}
 
 
@@ -157,9 +157,12 @@ def test_lanczos_6x6_projected_two_samples():
     np.testing.assert_allclose(to_complex(h2), w2, rtol=1e-5, atol=1e-4)
 
 
-@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("prec", [FP32, FP64, BF16X2, BF16X3])
 @pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[3], CASES[6]])
 def test_grad_logpsi(case, prec):
+    # BF16X2 / BF16X3: theta' from the tcgen05 GEMM, read by the gradient
+    # kernel; with two bf16 terms per weight (2^-17 relative each) O carries
+    # ~1e-5 relative error at weight scales >= 0.1, with three FP32 accuracy
     L, K, M, proj, inv, bias, mom, irr, std = case
     om, gm, _ = make_pair(L, K=K, M=M, proj=proj, spin_inv=inv, use_bias=bias, momentum=mom, irrep=irr,
                           std=std, precision=prec, logc_std=0.2 if K > 1 else None)
@@ -167,7 +170,8 @@ def test_grad_logpsi(case, prec):
     got = to_complex(gm.grad_logpsi(cfg_of(s)))
     want = om.grad_logpsi(s)
     scale = np.abs(want).max()
-    assert np.max(np.abs(got - want)) <= (1e-5 if prec == FP32 else 1e-10) * max(scale, 1.0)
+    tol = 1e-10 if prec == FP64 else 5e-5 if (prec == BF16X2 and std > 0.05) else 1e-5
+    assert np.max(np.abs(got - want)) <= tol * max(scale, 1.0)
 
 
 def test_energy_grad_and_sr_matvec_fp64():
