@@ -577,7 +577,8 @@ def profile_case(name):
       eloc6   E_loc, the 6x6 model, 2048 configurations
       sample6 the sampler, the 6x6 model, 76 chains x 4 samples (n_skip 10, n_burn 40)
       lz8     h1 and h2 of the 8x8 Lanczos model (M = 128, |G| = 512), 152 random Sz=0 configurations
-      cg10    the SR solve of the 10x10 K=4 model (P = 162004) over 1024 samples of random O, 5 CG iterations"""
+      cg10    the SR solve of the 10x10 K=4 model (P = 162004) over 1024 samples of random O, 5 CG iterations
+      grad10  O_k of the 10x10 K=4 model (tensor-core theta), 304 random Sz=0 configurations"""
     import torch
     from paper_2206_14307_gb300 import nnqs, synth
     if name == "cg10":
@@ -598,8 +599,8 @@ def profile_case(name):
         m.status()
         print(f"case {name}: {e0.elapsed_time(e1):.3f} ms", flush=True)
         return
-    if name == "tc10":
-        Lc, Mc, Kc, inv, n = 10, 400, 4, 0, 2048
+    if name in ("tc10", "grad10"):
+        Lc, Mc, Kc, inv, n = 10, 400, 4, 0, 2048 if name == "tc10" else 304
     elif name == "lz8":
         Lc, Mc, Kc, inv, n = LZ_L, LZ_M, 1, 0, 152
     else:
@@ -617,6 +618,9 @@ def profile_case(name):
         run = lambda: m.local_energy(cfg, out=out)
     elif name == "lz8":
         run = lambda: m.lanczos(cfg)
+    elif name == "grad10":
+        Ob = torch.empty(n, m.P, 2, dtype=torch.float64, device="cuda")
+        run = lambda: m.grad_logpsi(cfg, out=Ob)
     else:
         run = lambda: m.sample(14307, 76, 4, N_SKIP, 40)
     run()
@@ -648,7 +652,7 @@ def main():
     ap.add_argument("--sr-steps", type=int, default=1)
     ap.add_argument("--small", action="store_true",
                     help="128 chains and a 512-sample Lanczos leg (for profiler captures; not a bench line)")
-    ap.add_argument("--case", choices=["tc10", "tc6", "eloc6", "sample6", "lz8", "cg10"],
+    ap.add_argument("--case", choices=["tc10", "tc6", "eloc6", "sample6", "lz8", "cg10", "grad10"],
                     help="one small launch of one kernel for profiler captures (no bench line)")
     args = ap.parse_args()
     if args.case:

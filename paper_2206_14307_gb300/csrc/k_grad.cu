@@ -15,6 +15,23 @@
 
 namespace nnqs {
 
+constexpr int kGc = 16;   // rows g per staged chunk of the W-block GEMM
+
+__host__ __device__ __forceinline__ size_t grad_tg_bytes(int G, int N) { return ((size_t)G * N + 15) & ~(size_t)15; }
+
+// units a pass of the W-block GEMM covers (TM per thread slot)
+template <typename T> __host__ __device__ __forceinline__ int grad_mpass(int N)
+{
+    return (sizeof(T) == 4 ? 4 : 2) * (kThreads / ((N + 7) / 8));
+}
+
+template <typename T> size_t grad_smem_bytes(const DevModel<T> &md)
+{
+    const int nkb = (md.N + 7) / 8;
+    return grad_tg_bytes(md.G, md.N) + (size_t)kGc * grad_mpass<T>(md.N) * sizeof(cx<T>) +
+           (size_t)kGc * nkb * 8 * sizeof(T);
+}
+
 template <typename T> size_t grad_scratch_bytes(const DevModel<T> &md)
 {
     const size_t rows = (size_t)md.K * md.G;
@@ -29,6 +46,10 @@ __global__ void __launch_bounds__(kThreads) k_grad(DevModel<T> md, const uint64_
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int8_t *tg = reinterpret_cast<int8_t *>(smem_raw);  // [G][N]  (T_g s)_k
+    // staging of the W-block GEMM: kGc rows of U (4 units per thread slot) and
+    // of T_g s as floats (sites padded to 8)
+    cx<T> *us = reinterpret_cast<cx<T> *>(smem_raw + grad_tg_bytes(md.G, md.N));
+    T *ts = reinterpret_cast<T *>(us + (size_t)kGc * grad_mpass<T>(md.N));
     __shared__ T s_sm[kMaxN];
     __shared__ int8_t s8[kMaxN];
     __shared__ sc<T> wacc[kWarps];
@@ -186,24 +207,69 @@ __global__ void __launch_bounds__(kThreads) k_grad(DevModel<T> md, const uint64_
                     for (int g = 0; g < G; ++g) b = cadd(b, Vr[(size_t)g * M + m]);
                 Or[2 * (1 + N + m)] = (double)b.x; Or[2 * (1 + N + m) + 1] = (double)b.y;
             }
-            // W block: thread owns (m, 8 consecutive k)
-            const int kb = (N + 7) / 8;
-            for (int idx = threadIdx.x; idx < M * kb; idx += blockDim.x) {
-                const int m = idx % M, k0 = (idx / M) * 8;
-                cx<T> o[8];
+            // W block, O[W_r,m,k] = sum_g U_rgm (T_g s)_k: a register-tiled
+            // GEMM over g.  Thread (mi, ki) owns TM units x 8 sites (TM = 4 in
+            // FP32, 2 in FP64); a pass covers TM MI units, and chunks of kGc
+            // rows of U and of T_g s (as +-1 values) are staged in shared memory.
+            {
+                constexpr int TM = sizeof(T) == 4 ? 4 : 2;
+                const int nkb = (N + 7) / 8;
+                const int MI = kThreads / nkb;
+                const int mpass = grad_mpass<T>(N);   // TM MI
+                const int mi = (int)threadIdx.x % MI, ki = (int)threadIdx.x / MI;
+                const bool act = ki < nkb;
+                for (int mp = 0; mp < M; mp += mpass) {
+                    cx<T> o[TM][8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) o[q] = cx<T>{T(0), T(0)};
-                for (int g = 0; g < G; ++g) {
-                    const cx<T> u = Ur[(size_t)g * M + m];
-                    const int8_t *t = tg + g * N + k0;
+                    for (int a = 0; a < TM; ++a)
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (k0 + q < N) { const T tv = T(t[q]); o[q].x += tv * u.x; o[q].y += tv * u.y; }
+                        for (int q = 0; q < 8; ++q) o[a][q] = cx<T>{T(0), T(0)};
+                    for (int g0 = 0; g0 < G; g0 += kGc) {
+                        const int gc = G - g0 < kGc ? G - g0 : kGc;
+                        __syncthreads();
+                        for (int q = threadIdx.x; q < kGc * mpass; q += blockDim.x) {
+                            const int gg = q / mpass, mm = q - gg * mpass;
+                            cx<T> u{T(0), T(0)};
+                            if (gg < gc && mp + mm < M) u = Ur[(size_t)(g0 + gg) * M + mp + mm];
+                            us[q] = u;
+                        }
+                        for (int q = threadIdx.x; q < kGc * nkb * 8; q += blockDim.x) {
+                            const int gg = q / (nkb * 8), kk = q - gg * nkb * 8;
+                            ts[q] = (gg < gc && kk < N) ? T(tg[(g0 + gg) * N + kk]) : T(0);
+                        }
+                        __syncthreads();
+                        if (act) {
+                            for (int gg = 0; gg < gc; ++gg) {
+                                const cx<T> *ur = us + gg * mpass + TM * mi;
+                                const T *tr = ts + gg * nkb * 8 + 8 * ki;
+                                cx<T> u[TM];
+                                T tv[8];
+#pragma unroll
+                                for (int a = 0; a < TM; ++a) u[a] = ur[a];
+#pragma unroll
+                                for (int q = 0; q < 8; ++q) tv[q] = tr[q];
+#pragma unroll
+                                for (int a = 0; a < TM; ++a)
+#pragma unroll
+                                    for (int q = 0; q < 8; ++q) {
+                                        o[a][q].x += tv[q] * u[a].x;
+                                        o[a][q].y += tv[q] * u[a].y;
+                                    }
+                            }
+                        }
+                    }
+                    if (act) {
+#pragma unroll
+                        for (int a = 0; a < TM; ++a) {
+                            const int m = mp + TM * mi + a;
+                            if (m >= M) continue;
+                            double *ow = Or + 2 * (1 + N + M + (size_t)m * N + 8 * ki);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                if (8 * ki + q < N) { ow[2 * q] = (double)o[a][q].x; ow[2 * q + 1] = (double)o[a][q].y; }
+                        }
+                    }
                 }
-                double *ow = Or + 2 * (1 + N + M + (size_t)m * N + k0);
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (k0 + q < N) { ow[2 * q] = (double)o[q].x; ow[2 * q + 1] = (double)o[q].y; }
             }
         }
         __syncthreads();
@@ -222,7 +288,7 @@ cudaError_t launch_grad(const DevModel<T> &md, const uint64_t *cfg, int64_t n, d
 {
     if (n <= 0) return cudaSuccess;
     const int g = grid;
-    const size_t smem = (size_t)md.G * md.N;
+    const size_t smem = grad_smem_bytes(md);
     const size_t stride = grad_scratch_bytes(md);
     cudaError_t err = cudaSuccess;
     switch (mpl_slot(md.M)) {
