@@ -19,10 +19,10 @@ constexpr int kGc = 16;   // rows g per staged chunk of the W-block GEMM
 
 __host__ __device__ __forceinline__ size_t grad_tg_bytes(int G, int N) { return ((size_t)G * N + 15) & ~(size_t)15; }
 
-// units a pass of the W-block GEMM covers (TM per thread slot)
+// units a pass of the W-block GEMM covers (2 per thread slot)
 template <typename T> __host__ __device__ __forceinline__ int grad_mpass(int N)
 {
-    return (sizeof(T) == 4 ? 4 : 2) * (kThreads / ((N + 7) / 8));
+    return 2 * (kThreads / ((N + 7) / 8));
 }
 
 template <typename T> size_t grad_smem_bytes(const DevModel<T> &md)
@@ -40,7 +40,7 @@ template <typename T> size_t grad_scratch_bytes(const DevModel<T> &md)
 }
 
 template <typename T, int MPL>
-__global__ void __launch_bounds__(kThreads) k_grad(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
+__global__ void __launch_bounds__(kThreads, 2) k_grad(DevModel<T> md, const uint64_t *__restrict__ cfg, int64_t n,
                                                    double *__restrict__ O, unsigned char *__restrict__ scratch,
                                                    size_t scratch_stride, const float2 *__restrict__ th)
 {
@@ -110,10 +110,10 @@ __global__ void __launch_bounds__(kThreads) k_grad(DevModel<T> md, const uint64_
                     for (int i = lane; i < N; i += 32) { const cx<T> a = ar[pg[i]]; at.x += s_sm[i] * a.x; at.y += s_sm[i] * a.y; }
                     at = warp_sum(at);
                 }
-                cx<T> uacc[MPL], vacc[MPL];
-#pragma unroll
-                for (int j = 0; j < MPL; ++j) { uacc[j] = cx<T>{T(0), T(0)}; vacc[j] = cx<T>{T(0), T(0)}; }
+                // (U and V of the row are summed over the signs in the scratch
+                // rows themselves: no per-unit accumulators stay live)
                 cx<T> aacc{T(0), T(0)}, cacc{T(0), T(0)};
+                cx<T> *Urow = U + (size_t)row * M, *Vrow = V + (size_t)row * M;
                 for (int sg = 0; sg < md.nsign; ++sg) {
                     const int sign = sg ? -1 : 1;
                     cx<T> p[MPL];
@@ -155,21 +155,23 @@ __global__ void __launch_bounds__(kThreads) k_grad(DevModel<T> md, const uint64_
                         aacc = cadd(aacc, cscale(wt, T(sign)));
 #pragma unroll
                         for (int j = 0; j < MPL; ++j) {
-                            const cx<T> th = cx<T>{T(2) * p[j].x - T(1), T(2) * p[j].y};  // tanh
-                            const cx<T> wth = cmul(wt, th);
-                            vacc[j] = cadd(vacc[j], wth);
-                            uacc[j] = cadd(uacc[j], cscale(wth, T(sign)));
+                            const int m = lane + 32 * j;
+                            if (m < M) {
+                                const cx<T> th = cx<T>{T(2) * p[j].x - T(1), T(2) * p[j].y};  // tanh
+                                const cx<T> wth = cmul(wt, th);
+                                const cx<T> uw = cscale(wth, T(sign));
+                                if (sg == 0) {
+                                    Urow[m] = uw;
+                                    Vrow[m] = wth;
+                                } else {
+                                    Urow[m] = cadd(Urow[m], uw);
+                                    Vrow[m] = cadd(Vrow[m], wth);
+                                }
+                            }
                         }
                     }
                 }
-                if (pass == 1) {
-#pragma unroll
-                    for (int j = 0; j < MPL; ++j) {
-                        const int m = lane + 32 * j;
-                        if (m < M) { U[(size_t)row * M + m] = uacc[j]; V[(size_t)row * M + m] = vacc[j]; }
-                    }
-                    if (lane == 0) { A[row] = aacc; C[row] = cacc; }
-                }
+                if (pass == 1 && lane == 0) { A[row] = aacc; C[row] = cacc; }
             }
             if (pass == 0) {
                 if (lane == 0) wacc[warp] = acc;
@@ -208,11 +210,12 @@ __global__ void __launch_bounds__(kThreads) k_grad(DevModel<T> md, const uint64_
                 Or[2 * (1 + N + m)] = (double)b.x; Or[2 * (1 + N + m) + 1] = (double)b.y;
             }
             // W block, O[W_r,m,k] = sum_g U_rgm (T_g s)_k: a register-tiled
-            // GEMM over g.  Thread (mi, ki) owns TM units x 8 sites (TM = 4 in
-            // FP32, 2 in FP64); a pass covers TM MI units, and chunks of kGc
-            // rows of U and of T_g s (as +-1 values) are staged in shared memory.
+            // GEMM over g.  Thread (mi, ki) owns TM = 2 units x 8 sites (within
+            // the two-CTAs-per-SM register budget); a pass covers TM MI units,
+            // and chunks of kGc rows of U and of T_g s (as +-1 values) are
+            // staged in shared memory.
             {
-                constexpr int TM = sizeof(T) == 4 ? 4 : 2;
+                constexpr int TM = 2;
                 const int nkb = (N + 7) / 8;
                 const int MI = kThreads / nkb;
                 const int mpass = grad_mpass<T>(N);   // TM MI
