@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 const int t = t0 + tl;
                 const int row = md.nsign == 2 ? t >> 1 : t;
                 const int sg = t - row * md.nsign;
-                const int r = row / md.G, g = row - r * md.G;
+                const int r = md.K == 1 ? 0 : row / md.G, g = row - r * md.G;
                 const uint8_t *pg = md.perm + (size_t)g * N;
                 const int rs = r * 2 * N;
                 const float4 *Su = s4 + (size_t)(rs + sg * N + pg[iu]) * RF4 + gl;          // exp(-4 sigma W_u)
@@ -450,7 +450,18 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 }
                 ex += nrm(x, y);
                 const unsigned bal = __ballot_sync(0xffffffffu, big);
-                const sc<float> gq = group_prod<kCGL>(sc<float>{x, y, ex});
+                // product over the group's lanes (mantissas in [1, 2): one
+                // renormalisation per level)
+#pragma unroll
+                for (int o = kCGL / 2; o > 0; o >>= 1) {
+                    const float ox = shfl_x(x, o), oy = shfl_x(y, o);
+                    const int oe = __shfl_xor_sync(0xffffffffu, ex, o);
+                    const float nx = x * ox - y * oy;
+                    y = x * oy + y * ox;
+                    x = nx;
+                    ex += oe + nrm(x, y);
+                }
+                const sc<float> gq{x, y, ex};
                 if (gl == 0 && active) {
                     if (pending) { term[tl] = nterm[tl]; tpr[tl] = ntpr[tl]; }
                     if ((bal >> gbase) & 0xffu) bigf[tl] = 1;
@@ -465,7 +476,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 const int t = t0 + tl;
                 const int row = md.nsign == 2 ? t >> 1 : t;
                 const int sg = t - row * md.nsign;
-                const int r = row / md.G, g = row - r * md.G;
+                const int r = md.K == 1 ? 0 : row / md.G, g = row - r * md.G;
                 const int ku = md.perm[(size_t)g * N + iu], kd = md.perm[(size_t)g * N + id];
                 const int rs = r * 2 * N;
                 const sc<float> a = es[rs + sg * N + ku], b = es[rs + (sg ^ 1) * N + kd];
