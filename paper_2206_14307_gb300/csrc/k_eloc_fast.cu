@@ -36,11 +36,13 @@ constexpr int kEfGL = 8;             // lanes per row group
 constexpr int kEfMaxThreads = 512;   // at most 16 warps (128 registers per thread)
 
 struct EfArgs {
-    const float4 *tp;     // [K][2][NB][MH] paired per-bond tables U = 1 + T
+    const float4 *tp;     // [K][2] blocks of BS float4: [NB][MH] paired per-bond tables U = 1 + T
     const sc<float> *ep;  // [K][2][NB] e^{+C}, e^{-C}
-    int MH;               // unit pairs per table row (8 NP)
+    int MH;               // unit pairs per table row
+    int BS;               // float4 per (r, orientation) block: NB MH + padding
     int warps;
     int plain;            // 1: every row takes the plain factors (test hook)
+    int w_smem;           // 1: the weights W are staged in shared memory (sign-paired variant)
 };
 
 // The entries of one row and sign, 8 at a time: sum over the anti-aligned
@@ -384,21 +386,380 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
     }
 }
 
-// Paired tables from the connection tables of the model: tp[(r 2 + o) NB + b][k]
-// = (Ux_2k, Ux_2k+1, Uy_2k, Uy_2k+1), U = 1 + T, for unit pairs k < MH (U = 1
-// past M), and ep = e^{(1 - 2 o) C_b} as scaled numbers.
-__global__ void k_tables_paired(DevModel<float> md, int MH, float4 *__restrict__ tp, sc<float> *__restrict__ ep)
+// ---------------------------------------------------------------------------
+// Sign-paired variant (models with spin inversion): two groups of 4 lanes take
+// the two signs of one row.  They share the row's theta' (each lane computes
+// the unit pairs of one parity and swaps the other parity with its partner
+// lane), its images and the entry list; lane l owns the unit pairs
+// k = l + 4 j (j < NP), so that a row of 8 NP units has no padding when
+// M = 8 NP.  The (r, orientation) blocks of the tables are BS float4 apart,
+// an odd multiple of 64 bytes past NB MH, so that the pair's two 64-byte reads
+// of one entry (the same image bond in opposite orientations) fall in
+// different bank halves.
+// ---------------------------------------------------------------------------
+constexpr int kEpGL = 4;
+
+template <int NP, bool QF>
+__device__ __forceinline__ void ep_entries(const DevModel<float> &md, const float4 *tps, const sc<float> *eps,
+                                           const uint16_t *aa, const uint16_t *bps, int naa, int r, int sg, int MH,
+                                           int BS, const f2 (&ca)[NP], const f2 (&cb)[NP], const f2 (&cc)[NP],
+                                           int eref, int gl, int gbase, float &accx, float &accy, double &Ox,
+                                           double &Oy)
+{
+    const int NB = md.nbonds;
+    const f2 one2 = f2_pack(1.f, 1.f);
+    for (int e0 = 0; e0 < naa; e0 += kEpGL) {
+        const int e = e0 + gl;
+        int off = 0;
+        sc<float> pre{0.f, 0.f, 0};
+        if (e < naa) {
+            const uint16_t code = aa[e];
+            const int b = code & 0x7fff;
+            const uint16_t bp = bps[b];
+            const int bb = bp & 0x7fff;
+            const bool pos = ((code >> 15) != 0) != ((bp >> 15) != 0);
+            const int o = (pos != (sg != 0)) ? 0 : 1;
+            off = (r * 2 + o) * BS + bb * MH;
+            pre = eps[(r * 2 + o) * NB + bb];
+            const float c1 = 0.5f * bondJ(md, b);
+            pre.x *= c1;
+            pre.y *= c1;
+        }
+        float rx[kEpGL], ry[kEpGL];
+        int re[kEpGL];
+#pragma unroll
+        for (int q = 0; q < kEpGL; ++q) {
+            const float4 *trow = tps + __shfl_sync(0xffffffffu, off, gbase + q) + gl;
+            f2 Rx = one2, Ry = 0;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                f2 ux, uy;
+                lds128(trow + kEpGL * j, ux, uy);
+                f2 fx, fy;
+                if constexpr (QF) {
+                    fx = add2(ux, ca[j]);
+                    fy = add2(uy, cb[j]);
+                } else {
+                    const f2 tx = sub2(ux, one2);
+                    fx = fma2(cc[j], uy, fma2(ca[j], tx, one2));
+                    fy = fma2(ca[j], uy, mul2(cb[j], tx));
+                }
+                if (j == 0) {
+                    Rx = fx; Ry = fy;
+                } else {
+                    const f2 nx = sub2(mul2(Rx, fx), mul2(Ry, fy));
+                    Ry = fma2(Rx, fy, mul2(Ry, fx));
+                    Rx = nx;
+                }
+            }
+            float x = f2_lo(Rx) * f2_hi(Rx) - f2_lo(Ry) * f2_hi(Ry);
+            float y = f2_lo(Rx) * f2_hi(Ry) + f2_lo(Ry) * f2_hi(Rx);
+            re[q] = nrm(x, y);
+            rx[q] = x;
+            ry[q] = y;
+        }
+        // butterfly product-reduce-scatter over the group's 4 lanes
+#pragma unroll
+        for (int lev = 0; lev < 2; ++lev) {
+            const int o = 2 >> lev, cnt = 2 >> lev;
+            const bool upper = (gl & o) != 0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q < cnt) {
+                    const float sx = upper ? rx[q] : rx[q + cnt];
+                    const float sy = upper ? ry[q] : ry[q + cnt];
+                    const int se = upper ? re[q] : re[q + cnt];
+                    const float kx = upper ? rx[q + cnt] : rx[q];
+                    const float ky = upper ? ry[q + cnt] : ry[q];
+                    const int ke = upper ? re[q + cnt] : re[q];
+                    const float gx = __shfl_xor_sync(0xffffffffu, sx, o);
+                    const float gy = __shfl_xor_sync(0xffffffffu, sy, o);
+                    const int ge = __shfl_xor_sync(0xffffffffu, se, o);
+                    rx[q] = kx * gx - ky * gy;
+                    ry[q] = kx * gy + ky * gx;
+                    re[q] = ke + ge;
+                }
+            }
+        }
+        if (e < naa) {
+            const float vx = rx[0] * pre.x - ry[0] * pre.y, vy = rx[0] * pre.y + ry[0] * pre.x;
+            const int d = re[0] + pre.e + eref;
+            if (d > -100 && d < 100) {
+                const float f = __uint_as_float((uint32_t)(d + 127) << 23);
+                accx = fmaf(f, vx, accx);
+                accy = fmaf(f, vy, accy);
+            } else {
+                const double f = pow2i<double>(d);
+                Ox += f * (double)vx;
+                Oy += f * (double)vy;
+            }
+        }
+    }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kEfMaxThreads, 1)
+    k_eloc_pair(DevModel<float> md, EfArgs ea, const uint64_t *__restrict__ cfg, int64_t n, double *__restrict__ h1_out)
+{
+    constexpr int NH = (NP + 1) / 2;   // unit pairs of one parity per lane
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int NB = md.nbonds, K = md.K, MH = ea.MH, BS = ea.BS, N = md.N, M = md.M;
+    const int nwarps = blockDim.x >> 5, nrs = nwarps * 4;   // row slots: 4 per warp
+    float4 *tps = reinterpret_cast<float4 *>(smem);                                        // [K][2] x BS
+    float4 *wsv = tps + (size_t)K * 2 * BS;                                                // [K][N][M] W (if staged)
+    sc<float> *eps = reinterpret_cast<sc<float> *>(wsv + (ea.w_smem ? ((size_t)K * N * M + 1) / 2 : 0));   // [K][2][NB]
+    uint16_t *gbp = reinterpret_cast<uint16_t *>(eps + (size_t)K * 2 * NB);              // [nrs][NB]
+    uint8_t *gperm = reinterpret_cast<uint8_t *>(gbp + (size_t)nrs * NB);                 // [nrs][N]
+    __shared__ float s_sm[kMaxN];
+    __shared__ int8_t s8[kMaxN];
+    __shared__ uint16_t aa[4 * kMaxN];
+    __shared__ int n_aa;
+    __shared__ float diag_sh;
+    __shared__ sc<double> gsum[2][2 * 4 * (kEfMaxThreads / 32)];   // per (row slot, sign)
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> 2, gl = lane & 3, gbase = grp * 4;
+    const int pi = grp >> 1, sg = grp & 1, l8 = lane & 7;
+    const int rslot = warp * 4 + pi, gslot = rslot * 2 + sg;
+    uint8_t *pgs = gperm + (size_t)rslot * N;
+    uint16_t *bps = gbp + (size_t)rslot * NB;
+    const cx<float> *Wsrc = ea.w_smem ? reinterpret_cast<const cx<float> *>(wsv) : md.Wt;
+    const f2 zero2 = 0, mone2 = f2_pack(-1.f, -1.f);
+    const float sign = sg ? -1.f : 1.f;
+
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(ea.tp);
+        int4 *dst = reinterpret_cast<int4 *>(tps);
+        for (int q = threadIdx.x; q < K * 2 * BS; q += blockDim.x) dst[q] = src[q];
+        for (int q = threadIdx.x; q < K * 2 * NB; q += blockDim.x) eps[q] = ea.ep[q];
+        if (ea.w_smem) {
+            cx<float> *wd = reinterpret_cast<cx<float> *>(wsv);
+            for (int q = threadIdx.x; q < K * N * M; q += blockDim.x) wd[q] = md.Wt[q];
+        }
+    }
+
+    for (int64_t smp = blockIdx.x; smp < n; smp += gridDim.x) {
+        const uint64_t *w = cfg + smp * md.nwords;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int sv = spin_of(w, i);
+            s_sm[i] = (float)sv;
+            s8[i] = (int8_t)sv;
+        }
+        for (int q = threadIdx.x; q < 2 * 2 * nrs; q += blockDim.x) gsum[q / (2 * nrs)][q % (2 * nrs)] = sc<double>{0.0, 0.0, 0};
+        __syncthreads();
+        if (warp == 0) {
+            float d = 0.f;
+            int base = 0;
+            for (int b0 = 0; b0 < NB; b0 += 32) {
+                const int b = b0 + lane;
+                bool isaa = false;
+                int si = 0;
+                if (b < NB) {
+                    si = s8[md.bond_i[b]];
+                    const int sj = s8[md.bond_j[b]];
+                    d += 0.25f * bondJ(md, b) * (float)(si * sj);
+                    isaa = si != sj;
+                }
+                const unsigned bm = __ballot_sync(0xffffffffu, isaa);
+                if (isaa) aa[base + __popc(bm & ((1u << lane) - 1u))] = (uint16_t)(b | (si > 0 ? 0x8000 : 0));
+                base += __popc(bm);
+            }
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (lane == 0) { n_aa = base; diag_sh = d; }
+        }
+        __syncthreads();
+        const int naa = n_aa;
+
+        for (int rbase = 0; rbase < K * md.G; rbase += nrs) {
+            const bool active = rbase + rslot < K * md.G;
+            const int row = active ? rbase + rslot : 0;
+            const int r = K == 1 ? 0 : row / md.G, g = row - r * md.G;
+            __syncwarp();
+            for (int i = l8; i < N; i += 8) pgs[i] = md.perm[(size_t)g * N + i];
+            for (int b = l8; b < NB; b += 8) bps[b] = md.bperm[(size_t)g * NB + b];
+            __syncwarp();
+            // ---- theta': this lane's parity of unit pairs, then the partner's ----
+            float ox[2 * NH], oy[2 * NH];
+#pragma unroll
+            for (int u = 0; u < 2 * NH; ++u) { ox[u] = 0.f; oy[u] = 0.f; }
+            const cx<float> *Wr = Wsrc + (size_t)r * N * M;
+            for (int i = 0; i < N; ++i) {
+                const cx<float> *wk = Wr + (size_t)pgs[i] * M;
+                const float si = s_sm[i];
+#pragma unroll
+                for (int h = 0; h < NH; ++h) {
+                    const int jj = 2 * h + sg;
+                    const int m = 2 * (gl + kEpGL * jj);
+                    if ((M & 1) == 0 && m + 1 < M) {
+                        const float4 a = *reinterpret_cast<const float4 *>(wk + m);
+                        ox[2 * h] = fmaf(si, a.x, ox[2 * h]); oy[2 * h] = fmaf(si, a.y, oy[2 * h]);
+                        ox[2 * h + 1] = fmaf(si, a.z, ox[2 * h + 1]); oy[2 * h + 1] = fmaf(si, a.w, oy[2 * h + 1]);
+                    } else {
+                        if (m < M) { const cx<float> a = wk[m]; ox[2 * h] = fmaf(si, a.x, ox[2 * h]); oy[2 * h] = fmaf(si, a.y, oy[2 * h]); }
+                        if (m + 1 < M) { const cx<float> a = wk[m + 1]; ox[2 * h + 1] = fmaf(si, a.x, ox[2 * h + 1]); oy[2 * h + 1] = fmaf(si, a.y, oy[2 * h + 1]); }
+                    }
+                }
+            }
+            float tx[2 * NP], ty[2 * NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const int h = j >> 1;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const float vx = __shfl_xor_sync(0xffffffffu, ox[2 * h + u], 4);
+                    const float vy = __shfl_xor_sync(0xffffffffu, oy[2 * h + u], 4);
+                    const bool own = (j & 1) == sg;
+                    tx[2 * j + u] = own ? ox[2 * h + u] : vx;
+                    ty[2 * j + u] = own ? oy[2 * h + u] : vy;
+                }
+            }
+            cx<float> at{0.f, 0.f};
+            if (md.use_bias) {
+                const cx<float> *ar = md.avec + (size_t)r * N;
+                for (int i = l8; i < N; i += 8) { const cx<float> a = ar[pgs[i]]; at.x += s_sm[i] * a.x; at.y += s_sm[i] * a.y; }
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) {
+                    at.x += __shfl_xor_sync(0xffffffffu, at.x, o);
+                    at.y += __shfl_xor_sync(0xffffffffu, at.y, o);
+                }
+            }
+            // ---- this group's sign: p, q = 1/p - 1, the p product and the row term ----
+            f2 ca[NP], cb[NP], cc[NP];
+            sc<float> prod{1.f, 0.f, 0};
+            f2 Px = 0, Py = 0;
+            bool small = ea.plain != 0;
+            const cx<float> *br = md.bvec + (size_t)r * M;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                float pxv[2], pyv[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int m = 2 * (gl + kEpGL * j) + h;
+                    pxv[h] = 1.f; pyv[h] = 0.f;   // units past M: p = 1, q = 0 (their U is 1)
+                    if (m < M) {
+                        cx<float> th{sign * tx[2 * j + h], sign * ty[2 * j + h]};
+                        if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
+                        cx<float> mant, pv;
+                        int k;
+                        cosh2(th, mant, k, pv);
+                        pxv[h] = pv.x; pyv[h] = pv.y;
+                        const cx<float> q = cmul(mk(prod.x, prod.y), mant);
+                        prod = sc<float>{q.x, q.y, prod.e + k};
+                        small = small || !(pv.x * pv.x + pv.y * pv.y >= 0x1p-24f);
+                    }
+                }
+                const f2 px = f2_pack(pxv[0], pxv[1]), py = f2_pack(pyv[0], pyv[1]);
+                const f2 pden = fma2(px, px, mul2(py, py));
+                const f2 inv = f2_pack(__frcp_rn(f2_lo(pden)), __frcp_rn(f2_hi(pden)));
+                ca[j] = fma2(px, inv, mone2);              // q = 1/p - 1
+                cb[j] = mul2(sub2(zero2, py), inv);
+                cc[j] = px;   // (p kept for the plain form)
+                if (j == 0) {
+                    Px = px; Py = py;
+                } else {
+                    const f2 nx = sub2(mul2(Px, px), mul2(Py, py));
+                    Py = fma2(Px, py, mul2(Py, px));
+                    Px = nx;
+                }
+                (void)py;
+            }
+            prod = group_prod<kEpGL>(prod);
+            const cx<float> lc = md.logc[r];
+            sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
+            float chg = md.chi[g];
+            if (sg && md.chiP < 0) chg = -chg;
+            lead.x *= chg; lead.y *= chg;
+            const sc<float> wt = sc_mul(prod, sc_norm(lead));
+            if (gl == 0 && active) gsum[1][gslot] = sc_add(gsum[1][gslot], sc<double>{(double)wt.x, (double)wt.y, wt.e});
+
+            float accx = 0.f, accy = 0.f;
+            double Ox = 0.0, Oy = 0.0;
+            sc<float> mult;
+            if (!__any_sync(0xffffffffu, small)) {
+                const float u = f2_lo(Px) * f2_hi(Px) - f2_lo(Py) * f2_hi(Py);
+                const float v = f2_lo(Px) * f2_hi(Py) + f2_lo(Py) * f2_hi(Px);
+                const sc<float> Pp = group_prod<kEpGL>(sc<float>{u, v, 0});
+                ep_entries<NP, true>(md, tps, eps, aa, bps, naa, r, sg, MH, BS, ca, cb, cc, Pp.e, gl, gbase, accx,
+                                     accy, Ox, Oy);
+                mult = sc_mul(wt, sc<float>{Pp.x, Pp.y, 0});
+            } else {
+                // the plain factors 1 + p (U - 1): p from q (p = 1 / (1 + q)) would lose the
+                // small p, so take it from the kept copy and the product's imaginary parts
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    float pyv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int m = 2 * (gl + kEpGL * j) + h;
+                        pyv[h] = 0.f;
+                        if (m < M) {
+                            cx<float> th{sign * tx[2 * j + h], sign * ty[2 * j + h]};
+                            if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
+                            cx<float> mant, pv;
+                            int k;
+                            cosh2(th, mant, k, pv);
+                            pyv[h] = pv.y;
+                        }
+                    }
+                    ca[j] = cc[j];
+                    cb[j] = f2_pack(pyv[0], pyv[1]);
+                    cc[j] = f2_pack(-pyv[0], -pyv[1]);
+                }
+                ep_entries<NP, false>(md, tps, eps, aa, bps, naa, r, sg, MH, BS, ca, cb, cc, 0, gl, gbase, accx,
+                                      accy, Ox, Oy);
+                mult = wt;
+            }
+            double ax = (double)accx + Ox, ay = (double)accy + Oy;
+#pragma unroll
+            for (int o = kEpGL / 2; o > 0; o >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            }
+            if (gl == 0 && active) gsum[0][gslot] = sc_add(gsum[0][gslot], sd_mul(mult, ax, ay));
+        }
+        __syncthreads();
+        if (warp == 0) {
+            sc<double> t1{0.0, 0.0, 0}, t0{0.0, 0.0, 0};
+            for (int q = lane; q < 2 * nrs; q += 32) { t1 = sc_add(t1, gsum[0][q]); t0 = sc_add(t0, gsum[1][q]); }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const sc<double> u1{__shfl_xor_sync(0xffffffffu, t1.x, o), __shfl_xor_sync(0xffffffffu, t1.y, o),
+                                    __shfl_xor_sync(0xffffffffu, t1.e, o)};
+                const sc<double> u0{__shfl_xor_sync(0xffffffffu, t0.x, o), __shfl_xor_sync(0xffffffffu, t0.y, o),
+                                    __shfl_xor_sync(0xffffffffu, t0.e, o)};
+                t1 = sc_add(t1, u1);
+                t0 = sc_add(t0, u0);
+            }
+            if (lane == 0) {
+                const double den = t0.x * t0.x + t0.y * t0.y;
+                const double f = ldexp(1.0, t1.e - t0.e);
+                const double rx = (t1.x * t0.x + t1.y * t0.y) / den * f, ry = (t1.y * t0.x - t1.x * t0.y) / den * f;
+                const double h1x = (double)diag_sh + rx;
+                if (sc_zero(t0) || !isfinite(h1x) || !isfinite(ry)) flag_range(md.status);
+                h1_out[2 * smp] = h1x;
+                h1_out[2 * smp + 1] = ry;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Paired tables from the connection tables of the model: tp[(r 2 + o) BS + b MH
+// + k] = (Ux_2k, Ux_2k+1, Uy_2k, Uy_2k+1), U = 1 + T, for unit pairs k < MH
+// (U = 1 past M), and ep = e^{(1 - 2 o) C_b} as scaled numbers.
+__global__ void k_tables_paired(DevModel<float> md, int MH, int BS, float4 *__restrict__ tp, sc<float> *__restrict__ ep)
 {
     const int NB = md.nbonds;
     const int64_t tot = (int64_t)md.K * 2 * NB * MH;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rowi = q / MH;
+        const int64_t rowi = q / MH;                 // (r 2 + o) NB + b
         const int k = (int)(q - rowi * MH);
+        const int64_t blk = rowi / NB, b = rowi - blk * NB;
         const cx<float> *src = md.Tb + rowi * md.Mp;
         const int m0 = 2 * k, m1 = 2 * k + 1;
         const cx<float> a = m0 < md.M ? src[m0] : cx<float>{0.f, 0.f};
-        const cx<float> b = m1 < md.M ? src[m1] : cx<float>{0.f, 0.f};
-        tp[q] = make_float4(1.f + a.x, 1.f + b.x, a.y, b.y);
+        const cx<float> c = m1 < md.M ? src[m1] : cx<float>{0.f, 0.f};
+        tp[blk * BS + b * MH + k] = make_float4(1.f + a.x, 1.f + c.x, a.y, c.y);
     }
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)md.K * 2 * NB;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -413,21 +774,18 @@ __global__ void k_tables_paired(DevModel<float> md, int MH, float4 *__restrict__
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static int ef_np(int M) { return (M + 2 * kEfGL - 1) / (2 * kEfGL); }   // unit pairs per lane
+static int ef_np(int M) { return (M + 2 * kEfGL - 1) / (2 * kEfGL); }   // unit pairs per lane (8 lanes)
 
-// tables, prefactors and the per-group images of the bonds and sites under
-// the group's row
-static size_t ef_smem(const DevModel<float> &md, int warps)
-{
-    const int MH = kEfGL * ef_np(md.M);
-    return (size_t)md.K * 2 * md.nbonds * MH * sizeof(float4) + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) +
-           (size_t)warps * (32 / kEfGL) * (md.nbonds * sizeof(uint16_t) + md.N);
-}
+struct EfLayout {
+    bool pair;      // the sign-paired 4-lane kernel
+    int NP, MH, BS;
+    bool w_smem;    // W staged in shared memory (sign-paired kernel)
+};
 
 static int ef_warps(const DevModel<float> &md)
 {
-    // the most warps (latency hiding) whose row groups idle at most 1/8 of the
-    // time, else the count in 8..16 that idles least
+    // the most warps (latency hiding) whose row slots idle at most 1/8 of the
+    // time, else the count in 8..16 that idles least (4 row slots a warp)
     const int rows = md.K * md.G;
     int best = 16, waste = 1 << 30;
     for (int w = 16; w >= 8; --w) {
@@ -439,25 +797,63 @@ static int ef_warps(const DevModel<float> &md)
     return best;
 }
 
+// dynamic shared memory: tables, W (if staged), prefactors, the row slots'
+// images of the bonds and sites
+static size_t ef_smem(const DevModel<float> &md, const EfLayout &L, int warps)
+{
+    const size_t tab = (size_t)md.K * 2 * L.BS * sizeof(float4);
+    const size_t wst = L.w_smem ? ((size_t)md.K * md.N * md.M + 1) / 2 * sizeof(float4) : 0;
+    return tab + wst + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) +
+           (size_t)warps * 4 * (md.nbonds * sizeof(uint16_t) + md.N);
+}
+
+constexpr size_t kEfSmemLimit = 212 * 1024;   // dynamic part; the static part stays below 12 KB
+
+static EfLayout ef_layout(const DevModel<float> &md)
+{
+    EfLayout L{};
+    const int NB = md.nbonds;
+    const int npp = (md.M + 2 * kEpGL - 1) / (2 * kEpGL);
+    if (md.nsign == 2 && npp >= 1 && npp <= 10) {
+        L.pair = true;
+        L.NP = npp;
+        L.MH = kEpGL * npp;
+        const int64_t B = (int64_t)NB * L.MH;
+        const int res = (int)((4 * B) % 32);                 // 32-bit words mod the banks
+        L.BS = (int)(B + (((16 - res) % 32 + 32) % 32) / 4);  // blocks 16 words apart mod 32
+        L.w_smem = true;
+        if (ef_smem(md, L, ef_warps(md)) <= kEfSmemLimit) return L;
+        L.w_smem = false;
+        if (ef_smem(md, L, ef_warps(md)) <= kEfSmemLimit) return L;
+    }
+    L = EfLayout{};
+    L.NP = ef_np(md.M);
+    L.MH = kEfGL * L.NP;
+    L.BS = NB * L.MH;
+    return L;
+}
+
 bool eloc_fast_supported(const DevModel<float> &md)
 {
-    const int np = ef_np(md.M);
-    if (np < 1 || np > 8) return false;
-    return ef_smem(md, ef_warps(md)) <= 222 * 1024;   // with the static shared memory, within 227 KB
+    const EfLayout L = ef_layout(md);
+    if (L.pair) return true;
+    if (L.NP < 1 || L.NP > 8) return false;
+    return ef_smem(md, L, ef_warps(md)) <= kEfSmemLimit;
 }
 
 size_t eloc_fast_table_bytes(const DevModel<float> &md)
 {
-    const int MH = kEfGL * ef_np(md.M);
-    return (size_t)md.K * 2 * md.nbonds * MH * sizeof(float4) + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) + 256;
+    const EfLayout L = ef_layout(md);
+    return (size_t)md.K * 2 * L.BS * sizeof(float4) + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) + 256;
 }
 
 cudaError_t launch_tables_paired(const DevModel<float> &md, void *tables, cudaStream_t st)
 {
-    const int MH = kEfGL * ef_np(md.M);
+    const EfLayout L = ef_layout(md);
     float4 *tp = reinterpret_cast<float4 *>(tables);
-    sc<float> *ep = reinterpret_cast<sc<float> *>(tp + (size_t)md.K * 2 * md.nbonds * MH);
-    k_tables_paired<<<256, 256, 0, st>>>(md, MH, tp, ep);
+    sc<float> *ep = reinterpret_cast<sc<float> *>(tp + (size_t)md.K * 2 * L.BS);
+    if (L.BS != md.nbonds * L.MH) cudaMemsetAsync(tp, 0, (size_t)md.K * 2 * L.BS * sizeof(float4), st);
+    k_tables_paired<<<256, 256, 0, st>>>(md, L.MH, L.BS, tp, ep);
     return cudaGetLastError();
 }
 
@@ -465,28 +861,45 @@ cudaError_t launch_eloc_fast(const DevModel<float> &md, const void *tables, cons
                              double *h1, int nsm, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
+    const EfLayout L = ef_layout(md);
     EfArgs ea;
-    const int np = ef_np(md.M);
-    ea.MH = kEfGL * np;
+    ea.MH = L.MH;
+    ea.BS = L.BS;
+    ea.w_smem = L.w_smem;
     ea.tp = reinterpret_cast<const float4 *>(tables);
-    ea.ep = reinterpret_cast<const sc<float> *>(ea.tp + (size_t)md.K * 2 * md.nbonds * ea.MH);
+    ea.ep = reinterpret_cast<const sc<float> *>(ea.tp + (size_t)md.K * 2 * L.BS);
     ea.warps = ef_warps(md);
-    // Test hook (unset in normal use): NNQS_TEST_ELOC_PLAIN=1 takes the plain
+    // Test hooks (unset in normal use): NNQS_TEST_ELOC_PLAIN=1 takes the plain
     // factors 1 + p (U - 1) in every row.
     const char *hook = getenv("NNQS_TEST_ELOC_PLAIN");
     ea.plain = hook && hook[0] == '1';
-    const size_t smem = ef_smem(md, ea.warps);
+    const size_t smem = ef_smem(md, L, ea.warps);
     const int grid = (int)(n < nsm ? n : nsm);
     void (*kern)(DevModel<float>, EfArgs, const uint64_t *, int64_t, double *) = nullptr;
-    switch (np) {
-    case 1: kern = k_eloc_fast<1>; break;
-    case 2: kern = k_eloc_fast<2>; break;
-    case 3: kern = k_eloc_fast<3>; break;
-    case 4: kern = k_eloc_fast<4>; break;
-    case 5: kern = k_eloc_fast<5>; break;
-    case 6: kern = k_eloc_fast<6>; break;
-    case 7: kern = k_eloc_fast<7>; break;
-    default: kern = k_eloc_fast<8>; break;
+    if (L.pair) {
+        switch (L.NP) {
+        case 1: kern = k_eloc_pair<1>; break;
+        case 2: kern = k_eloc_pair<2>; break;
+        case 3: kern = k_eloc_pair<3>; break;
+        case 4: kern = k_eloc_pair<4>; break;
+        case 5: kern = k_eloc_pair<5>; break;
+        case 6: kern = k_eloc_pair<6>; break;
+        case 7: kern = k_eloc_pair<7>; break;
+        case 8: kern = k_eloc_pair<8>; break;
+        case 9: kern = k_eloc_pair<9>; break;
+        default: kern = k_eloc_pair<10>; break;
+        }
+    } else {
+        switch (L.NP) {
+        case 1: kern = k_eloc_fast<1>; break;
+        case 2: kern = k_eloc_fast<2>; break;
+        case 3: kern = k_eloc_fast<3>; break;
+        case 4: kern = k_eloc_fast<4>; break;
+        case 5: kern = k_eloc_fast<5>; break;
+        case 6: kern = k_eloc_fast<6>; break;
+        case 7: kern = k_eloc_fast<7>; break;
+        default: kern = k_eloc_fast<8>; break;
+        }
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
