@@ -450,8 +450,9 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 }
                 ex += nrm(x, y);
                 const unsigned bal = __ballot_sync(0xffffffffu, big);
-                // product over the group's lanes (mantissas in [1, 2): one
-                // renormalisation per level)
+                // product over the group's 8 lanes: the mantissas are in [1, 2), so
+                // the product's stays below 2^8 with no renormalisation (the term
+                // pass normalises it)
 #pragma unroll
                 for (int o = kCGL / 2; o > 0; o >>= 1) {
                     const float ox = shfl_x(x, o), oy = shfl_x(y, o);
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                     const float nx = x * ox - y * oy;
                     y = x * oy + y * ox;
                     x = nx;
-                    ex += oe + nrm(x, y);
+                    ex += oe;
                 }
                 const sc<float> gq{x, y, ex};
                 if (gl == 0 && active) {
