@@ -31,6 +31,11 @@ __device__ __forceinline__ void lds128(const void *p, f2 &a, f2 &b)
     const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
     asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }
+// the same at a shared-memory address
+__device__ __forceinline__ void lds128(uint32_t addr, f2 &a, f2 &b)
+{
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
 __device__ __forceinline__ f2 sub2(f2 a, f2 b)
 {
     f2 d;

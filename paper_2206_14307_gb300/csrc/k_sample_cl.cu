@@ -1,22 +1,32 @@
 // k_sample_cl.cu -- Metropolis sampler (Sec. 3.2) with each chain's cache in the
 // shared memory of a thread-block cluster (FP32).
 //
-// Same chain, proposals, acceptance rule and cache arithmetic as k_sample.cu:
-// for every (row, sign) pair t of the projected sum the chain keeps
-// p_m = e^theta/(2cosh theta) per hidden unit and the pair's term; a proposed
-// exchange of an up site u and a down site d changes pair t by
-// exp(sigma C_ud) prod_m (1 + p_m T_m), T_m = exp(-4 sigma (W_m,g(u) - W_m,g(d))) - 1.
+// Same chain, proposals and acceptance rule as k_sample.cu.  A proposed
+// exchange of an up site u and a down site d changes the hidden angle of unit m
+// of the (row, sign) pair (r, g, sigma) by sigma delta_m, and the pair's term by
+// exp(sigma C_ud) prod_m cosh(theta_m + sigma delta_m) / cosh(theta_m), with
+// U_m = e^{2 delta_m} = exp(-4 (W_m,g(u) - W_m,g(d))) the same for both signs.
 //
-// Here the pairs of one chain are split over the CL CTAs of a cluster (one
-// CTA per SM), each holding its pairs' p and the per-site tables exp(-+4W)
-// in shared memory (no L1/L2 round trip per proposal).  A step is: the proposal (every CTA draws the same Philox
-// words), one pass over the CTA's pairs, the CTA's sums of old and new terms,
-// an exchange of those sums through distributed shared memory and one cluster
-// barrier, and the acceptance decision (every CTA adds the CL partial sums in
-// rank order and reaches the same decision).  An accepted exchange is applied
-// in place -- p' = p (1 + T)/(1 + p T), term' = term * ratio -- at the start of
-// the next step's pass, so no speculative second buffer is needed and p is
-// read once per step.
+// Cache.  Per pair the chain keeps, per unit, c_m = e^{-2 theta'_m} with
+// theta' = -theta for sigma = +1 and theta' = theta for sigma = -1, and the
+// scalar tc = term x prod_m p(theta'_m), p(x) = e^x / (2 cosh x).  In this form
+// the unit factor of both signs is (1 + c_m U_m) -- for sigma = +1 it is
+// 1 + p(theta)(U - 1) = p(theta') (1 + c U), for sigma = -1 it is
+// p(theta')(1 + c U) / U -- so
+//   new term = tc x e^{sigma C_ud} x prod_m (1 + c_m U_m) x X,
+//   X = 1 (sigma = +1) or prod_m 1/U_m = e^{4 (CS_g(u) - CS_g(d))} (sigma = -1),
+// and an accepted exchange multiplies every c_m of both signs by U_m and tc by
+// e^{sigma C_ud} X.  The two signs of a row read the same site factors.
+//
+// Layout.  The rows of the chain are split over the CL CTAs of a cluster (one
+// CTA per SM); each CTA holds its rows' c, the per-site factors exp(-+4W) and
+// the per-pair scalars in shared memory.  A group of 8 lanes takes a row: one
+// pass reads the site factors of the proposal (and, after an acceptance, of
+// the accepted exchange, applied to c in place), forms prod_m (1 + c_m U_m) of
+// both signs and the row's new terms.  The CTA's sums of old and new terms go
+// to every CTA of the cluster through distributed shared memory; after one
+// cluster barrier every CTA adds the CL partial sums in rank order and reaches
+// the same decision.
 #include "common.cuh"
 #include "f2.cuh"
 #include "kernels.h"
@@ -24,7 +34,7 @@
 namespace nnqs {
 
 constexpr int kCGL = 8;              // lanes per pair group
-constexpr int kClMaxThreads = 640;   // at most 20 warps
+constexpr int kClMaxThreads = 576;   // at most 18 warps
 
 __device__ __forceinline__ uint32_t cluster_rank()
 {
@@ -57,13 +67,6 @@ __device__ __forceinline__ void st_cluster_f32(const void *local, uint32_t rank,
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
 }
 
-__device__ __forceinline__ float rcp_nr_f(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return fmaf(r, fmaf(-x, r, 1.0f), r);
-}
-
 // k-th set bit (0-based) of a multi-word mask
 __device__ __forceinline__ int kth_set(const uint64_t *w, int nwords, int k)
 {
@@ -82,35 +85,71 @@ __device__ __forceinline__ int kth_set(const uint64_t *w, int nwords, int k)
 
 struct ClPlan {
     int CL;        // CTAs per cluster (1, 2, 4, 8)
-    int TP;        // pairs per CTA
+    int TR;        // rows per CTA (each with its nsign pairs)
     int threads;   // threads per CTA (multiple of 32)
     size_t smem;   // dynamic shared memory per CTA
 };
 
-// Shared memory of one CTA: site factor rows u = exp(-+4W) [K][2][N] and the
-// chain's q rows [TP] (64 MPL bytes a row, see below), per pair the term,
-// term x prod_m p_m and their values after an accepted proposal, site
+// Shared memory of one CTA: site factor rows u = exp(-+4W) [K][2][N], the
+// chain's c rows of sign +1 [TR] and, for models with spin inversion, the
+// rows e^{-4 b} [K] (64 MPL bytes a row, see below); per pair tc, in two
+// buffers (the current one and its value after an acceptance); site
 // prefactors e^{+-Cs} and the products of u over the units e^{-+4 CS}
-// [K][2][N] each, exchange slots [2][CL][8], a flag byte per pair.
-static size_t cl_smem(const DevModel<float> &md, int TP, int CL, int MPL)
+// [K][2][N] each, exchange slots [2][CL][4], a flag byte per row.
+static size_t cl_smem(const DevModel<float> &md, int TR, int CL, int MPL)
 {
-    return (size_t)(md.K * 2 * md.N + TP) * 64 * MPL + 4 * (size_t)TP * sizeof(sc<float>) +
-           2 * (size_t)md.K * 2 * md.N * sizeof(sc<float>) + 2 * (size_t)CL * 8 * sizeof(float) + (size_t)TP;
+    const size_t rows = (size_t)md.K * 2 * md.N + TR + (md.nsign == 2 ? md.K : 0);
+    return rows * 64 * MPL + 2 * (size_t)TR * md.nsign * sizeof(sc<float>) +
+           2 * (size_t)md.K * 2 * md.N * sizeof(sc<float>) + 2 * (size_t)CL * 4 * sizeof(float) + (size_t)TR;
 }
 
-// Sums over the warp of two scaled complex numbers: v = (sum a, sum b) as plain
-// FP32 numbers times 2^e, e the largest exponent in the warp (zeros ignored).
-__device__ __forceinline__ int warp_scaled(sc<float> a, sc<float> b, float (&v)[4])
+// Sum over the warp of a scaled complex number: v = sum a as a plain FP32
+// number times 2^e, e the largest exponent in the warp (zeros ignored).
+__device__ __forceinline__ int warp_scaled(sc<float> a, float (&v)[2])
 {
-    const int ea = sc_zero(a) ? -(1 << 28) : a.e, eb = sc_zero(b) ? -(1 << 28) : b.e;
-    const int e = __reduce_max_sync(0xffffffffu, ea > eb ? ea : eb);
-    const float fa = pow2i<float>(a.e - e), fb = pow2i<float>(b.e - e);
-    v[0] = a.x * fa; v[1] = a.y * fa; v[2] = b.x * fb; v[3] = b.y * fb;
+    const int e = __reduce_max_sync(0xffffffffu, sc_zero(a) ? -(1 << 28) : a.e);
+    const float f = pow2i<float>(a.e - e);
+    v[0] = a.x * f; v[1] = a.y * f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        v[1] += __shfl_xor_sync(0xffffffffu, v[1], o);
+    }
     return e;
+}
+
+// The sum of v over every thread of the cluster's CTAs (called by all
+// threads; the result is valid in thread 0).  Warp sums, one sum per CTA,
+// sent to every CTA's slot [rank] through distributed shared memory, one
+// cluster barrier, and the CL partial sums added in rank order, so that every
+// CTA gets the same number.
+__device__ __forceinline__ sc<float> cluster_sum(sc<float> v, sc<float> *wsum, float *slots, int CL, uint32_t rank)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    {
+        float w[2];
+        const int e = warp_scaled(v, w);
+        if (lane == 0) wsum[warp] = sc<float>{w[0], w[1], e};
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float w[2];
+        const int e = warp_scaled(lane < nwarps ? wsum[lane] : sc<float>{0.f, 0.f, 0}, w);
+        const sc<float> a = sc_norm(sc<float>{w[0], w[1], e});
+        if (CL == 1) {
+            if (lane == 0) { slots[0] = a.x; slots[1] = a.y; slots[2] = __int_as_float(a.e); }
+        } else if (lane < CL) {   // lane q writes into CTA q's slot [rank]
+            st_cluster_f32(slots + rank * 4 + 0, (uint32_t)lane, a.x);
+            st_cluster_f32(slots + rank * 4 + 1, (uint32_t)lane, a.y);
+            st_cluster_f32(slots + rank * 4 + 2, (uint32_t)lane, __int_as_float(a.e));
+        }
+    }
+    if (CL > 1) cluster_sync();
+    else __syncthreads();
+    sc<float> t{0.f, 0.f, 0};
+    if (threadIdx.x == 0)
+        for (int q = 0; q < CL; ++q) t = sc_add(t, sc<float>{slots[q * 4], slots[q * 4 + 1], __float_as_int(slots[q * 4 + 2])});
+    return t;
 }
 
 // units per lane of a width M (the kernel's variants)
@@ -126,30 +165,30 @@ constexpr size_t kClSmemLimit = 224 * 1024;   // dynamic shared memory of one CT
 static ClPlan cl_plan(const DevModel<float> &md, int force_cl)
 {
     ClPlan p{0, 0, 0, 0};
-    const int nrs = md.K * md.G * md.nsign;
+    const int nrows = md.K * md.G;
     for (int CL = 1; CL <= 8; CL *= 2) {
         if (force_cl > 0 && CL != force_cl) continue;
-        const int TP = (nrs + CL - 1) / CL;
-        const size_t s = cl_smem(md, TP, CL, cl_mpl(md.M));
+        const int TR = (nrows + CL - 1) / CL;
+        const size_t s = cl_smem(md, TR, CL, cl_mpl(md.M));
         if (s <= kClSmemLimit) {
-            p.CL = CL; p.TP = TP; p.smem = s;
+            p.CL = CL; p.TR = TR; p.smem = s;
             break;
         }
     }
     if (!p.CL) return p;
-    // warps: the count in 8..20 that leaves the fewest idle pair groups
+    // warps: the count in 8..18 that leaves the fewest idle row groups
     int best_w = 16, best_waste = 1 << 30;
-    for (int w = 20; w >= 8; --w) {
+    for (int w = kClMaxThreads / 32; w >= 8; --w) {
         const int slots = 4 * w;
-        const int waste = (p.TP + slots - 1) / slots * slots - p.TP;
+        const int waste = (p.TR + slots - 1) / slots * slots - p.TR;
         if (waste < best_waste) { best_waste = waste; best_w = w; }
     }
     p.threads = 32 * best_w;
     return p;
 }
 
-// Row layout of the site factor rows and the chain's q rows: lane gl of a
-// pair group owns the units m = gl + 8 j (j < MPL); the units (j, j + 1) of
+// Row layout of the site factor rows and the chain's c rows: lane gl of a
+// row group owns the units m = gl + 8 j (j < MPL); the units (j, j + 1) of
 // even j < MPL - 1 sit in one float4 (x_j, x_j+1, y_j, y_j+1) at float4 index
 // (j / 2) 8 + gl, so that a group reads 128 contiguous bytes per step; for odd
 // MPL the last unit is a float2 at float2 index (MPL - 1) 8 + gl.  A row is
@@ -167,55 +206,64 @@ template <int MPL> __device__ __forceinline__ void row_offsets(int j, int gl, in
     }
 }
 
-__device__ __forceinline__ void lds64(const void *p, float &x, float &y)
+__device__ __forceinline__ void lds64(uint32_t addr, float &x, float &y)
 {
-    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(addr));
 }
-__device__ __forceinline__ void sts128(void *p, f2 a, f2 b)
+__device__ __forceinline__ void sts128(uint32_t addr, f2 a, f2 b)
 {
-    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
     asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
 }
+__device__ __forceinline__ void sts64(uint32_t addr, float x, float y)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(x), "f"(y) : "memory");
+}
 
-template <int MPL>
+template <int MPL, int NS>
 __global__ void __launch_bounds__(kClMaxThreads, 1)
     k_sample_cl(DevModel<float> md, uint64_t seed, int n_chains, int n_per_chain, int n_skip, int n_burn,
-                uint64_t *__restrict__ cfg_out, float *__restrict__ acc_out, int CL, int TP)
+                uint64_t *__restrict__ cfg_out, float *__restrict__ acc_out, int CL, int TR)
 {
     constexpr int NG = 32 / kCGL;
     constexpr int NPAIR = MPL / 2, SGL = MPL & 1;
-    constexpr int RF4 = 4 * MPL;   // float4 per row
+    constexpr int RF4 = 4 * MPL;                   // float4 per row
+    constexpr bool BREG = NS == 2 && MPL <= 9;     // e^{-4b} of the lane's units kept in registers
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_sm[kMaxN];
     __shared__ uint64_t upm[kMaxWords], dnm[kMaxWords];
-    __shared__ sc<float> wold[32], wnew[32];
-    __shared__ int site_u, site_d, pend, pend_u, pend_d;
-    __shared__ uint32_t wnext[3];
-    __shared__ float u_sh;
+    __shared__ sc<float> wsum[32];
+    __shared__ sc<float> s_cur;      // the sum of the current terms (thread 0)
+    __shared__ int pend, pend_u, pend_d, tsel;
+    __shared__ int cand[4];          // the next proposal (u, d) if this one is rejected, then if accepted
+    __shared__ uint32_t wnx[2][3];   // Philox words of the steps, by parity
+    __shared__ int s_b2;             // max(1, max_m |e^{-4b_m}|^2), FP32 bits
 
     const int M = md.M, N = md.N;
-    float4 *s4 = reinterpret_cast<float4 *>(smem);                              // [K][2][N] rows of u = exp(-+4W)
-    float4 *qc = s4 + (size_t)md.K * 2 * N * RF4;                               // [TP] rows of q = (1 - p)/p
-    sc<float> *term = reinterpret_cast<sc<float> *>(qc + (size_t)TP * RF4);     // [TP] the pair's term
-    sc<float> *tpr = term + TP;                                                 // [TP] term x prod_m p_m
-    sc<float> *nterm = tpr + TP;                                                // [TP] prod (q + U), then the new term
-    sc<float> *ntpr = nterm + TP;                                               // [TP] tpr after an accepted proposal
-    sc<float> *es = ntpr + TP;                                                  // [K][2][N] site prefactors e^{+-Cs}
-    sc<float> *ec = es + (size_t)md.K * 2 * N;                                  // [K][2][N] prod_m u_m = e^{-+4 CS}
-    float *xch = reinterpret_cast<float *>(ec + (size_t)md.K * 2 * N);          // [2][CL][8]
-    // [TP] per pair: some |q| of the pair may exceed 2^12, so that its running
+    const int TP = TR * NS;
+    float4 *s4 = reinterpret_cast<float4 *>(smem);                               // [K][2][N] rows of u = exp(-+4W)
+    float4 *cc = s4 + (size_t)md.K * 2 * N * RF4;                                // [TR] rows of c (sign +1)
+    float4 *bt = cc + (size_t)TR * RF4;                                          // [K] rows of e^{-4b} (NS = 2)
+    sc<float> *tcb = reinterpret_cast<sc<float> *>(bt + (NS == 2 ? (size_t)md.K * RF4 : 0));   // [2][TP] tc
+    sc<float> *es = tcb + 2 * TP;                                                // [K][2][N] site prefactors e^{+-Cs}
+    sc<float> *ec = es + (size_t)md.K * 2 * N;                                   // [K][2][N] prod_m u_m = e^{-+4 CS}
+    float *xch = reinterpret_cast<float *>(ec + (size_t)md.K * 2 * N);           // [2][CL][4]
+    // [TR] per row: some |c| of the row may exceed 2^12, so that its running
     // products are renormalised after every unit pair
-    uint8_t *bigf = reinterpret_cast<uint8_t *>(xch + 2 * CL * 8);
+    uint8_t *bigf = reinterpret_cast<uint8_t *>(xch + 2 * CL * 4);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int grp = lane / kCGL, gl = lane % kCGL, gbase = grp * kCGL;
     const int slot = warp * NG + grp, nslots = nwarps * NG;
-    const int nrs = md.K * md.G * md.nsign;
+    const int nrows = md.K * md.G;
     const uint32_t rank = cluster_rank();
-    const int t0 = (int)rank * TP;
-    const int ntp = t0 >= nrs ? 0 : (nrs - t0 < TP ? nrs - t0 : TP);
-    uint32_t gstep = 0;   // steps of this cluster over all its chains (parity of the exchange slots)
+    const int r0 = (int)rank * TR;
+    const int ntr = r0 >= nrows ? 0 : (nrows - r0 < TR ? nrows - r0 : TR);
+    const f2 one2 = f2_pack(1.f, 1.f), mone2 = f2_pack(-1.f, -1.f);
+    const uint32_t a_s4 = (uint32_t)__cvta_generic_to_shared(s4), a_cc = (uint32_t)__cvta_generic_to_shared(cc),
+                   a_bt = (uint32_t)__cvta_generic_to_shared(bt);
+    uint32_t gstep = 0;   // exchanges of this cluster (parity of the exchange slots)
+    if (threadIdx.x == 0) s_b2 = __float_as_int(1.f);
+    __syncthreads();
     {
         float *s4f = reinterpret_cast<float *>(s4);
         for (int q = threadIdx.x; q < md.K * 2 * N * 8 * MPL; q += blockDim.x) {
@@ -227,6 +275,28 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
             s4f[(size_t)row * 8 * MPL * 2 + ore] = v.x;
             s4f[(size_t)row * 8 * MPL * 2 + oim] = v.y;
         }
+        if (NS == 2) {
+            float *btf = reinterpret_cast<float *>(bt);
+            for (int q = threadIdx.x; q < md.K * 8 * MPL; q += blockDim.x) {
+                const int r = q / (8 * MPL), w = q - r * 8 * MPL;
+                const int l = w % 8, j = w / 8, m = l + 8 * j;
+                cx<float> v{1.f, 0.f};
+                if (m < M && md.use_bias) {
+                    const cx<float> b = md.bvec[(size_t)r * M + m];
+                    // |e^{-4b}| must stay a normal FP32 number
+                    if (!(fabsf(b.x) <= 20.f)) flag_range(md.status);
+                    float sn, cs;
+                    sincosf(-4.f * b.y, &sn, &cs);
+                    const float mg = expf(-4.f * b.x);
+                    v = cx<float>{mg * cs, mg * sn};
+                    atomicMax(&s_b2, __float_as_int(v.x * v.x + v.y * v.y));   // non-negative: ordered as integers
+                }
+                int ore, oim;
+                row_offsets<MPL>(j, l, ore, oim);
+                btf[(size_t)r * 8 * MPL * 2 + ore] = v.x;
+                btf[(size_t)r * 8 * MPL * 2 + oim] = v.y;
+            }
+        }
         for (int q = threadIdx.x; q < md.K * 2 * N; q += blockDim.x) {
             es[q] = md.ES[q];
             const int rk = q / (2 * N), o = (q / N) & 1, k = q % N;
@@ -236,6 +306,15 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
         }
     }
     __syncthreads();
+    // a row is flagged big when some |c| of sign +1 or -1 exceeds 2^12, i.e.
+    // when some |c(+1)|^2 exceeds c0lim
+    const float c0lim = 0x1p24f / __int_as_float(s_b2);
+    // e^{-4b} of the lane's units for the RBM rcur (loaded when a row of another RBM comes)
+    int rcur = -1;
+    f2 bx[BREG ? NPAIR : 1], by[BREG ? NPAIR : 1];
+    float bsx = 1.f, bsy = 0.f;
+#pragma unroll
+    for (int i = 0; i < (BREG ? NPAIR : 1); ++i) { bx[i] = one2; by[i] = 0; }
 
     for (int chain = (int)cluster_id_x(); chain < n_chains; chain += (int)cluster_count_x()) {
         const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ (uint32_t)chain;
@@ -257,32 +336,38 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 if (s8[i] > 0) upm[i >> 6] |= 1ull << (i & 63);
                 else dnm[i >> 6] |= 1ull << (i & 63);
             }
+            // the first proposal, in the initial configuration
+            const u32x4 w0 = philox(0u, 0u, 0u, 0u, k0, k1);
+            wnx[0][0] = w0.v[0]; wnx[0][1] = w0.v[1]; wnx[0][2] = w0.v[2];
+            cand[0] = kth_set(upm, md.nwords, (int)(((uint64_t)w0.v[0] * (uint64_t)(N / 2)) >> 32));
+            cand[1] = kth_set(dnm, md.nwords, (int)(((uint64_t)w0.v[1] * (uint64_t)(N / 2)) >> 32));
+            pend = 0; pend_u = 0; pend_d = 0;   // no exchange to apply before the first step
+            tsel = 0;
         }
         __syncthreads();
 
-        // ---- fresh cache of this CTA's pairs: q = 1/p - 1 per unit, the term
-        //      and term x prod_m p_m per pair ----
-        for (int tb = 0; tb < ntp; tb += nslots) {
-            const int tl0 = tb + slot;
-            const bool active = tl0 < ntp;
-            const int tl = active ? tl0 : 0;
-            const int t = t0 + tl;
-            const int row = md.nsign == 2 ? t >> 1 : t;
-            const int sg = t - row * md.nsign;
-            const int sign = sg ? -1 : 1;
+        // ---- fresh cache of this CTA's rows: c = 1/p(theta') - 1 per unit of
+        //      sign +1, tc per pair, and the chain's sum of terms ----
+        sc<float> so{0.f, 0.f, 0};
+        for (int tb = 0; tb < ntr; tb += nslots) {
+            const int rl0 = tb + slot;
+            const bool active = rl0 < ntr;
+            const int rl = active ? rl0 : 0;
+            const int row = r0 + rl;
             const int r = row / md.G, g = row - r * md.G;
             const uint8_t *pg = md.perm + (size_t)g * N;
             const cx<float> *Wr = md.Wt + (size_t)r * N * M;
-            cx<float> thp[MPL];
+            cx<float> xs[MPL];   // sum_i W_m,g(i) s_i of the lane's units
 #pragma unroll
-            for (int j = 0; j < MPL; ++j) thp[j] = cx<float>{0.f, 0.f};
+            for (int j = 0; j < MPL; ++j) xs[j] = cx<float>{0.f, 0.f};
+#pragma unroll 2
             for (int i = 0; i < N; ++i) {
                 const cx<float> *wk = Wr + (size_t)pg[i] * M;
                 const float si = s_sm[i];
 #pragma unroll
                 for (int j = 0; j < MPL; ++j) {
                     const int m = gl + kCGL * j;
-                    if (m < M) { const cx<float> w = wk[m]; thp[j].x += si * w.x; thp[j].y += si * w.y; }
+                    if (m < M) { const cx<float> w = wk[m]; xs[j].x += si * w.x; xs[j].y += si * w.y; }
                 }
             }
             cx<float> at{0.f, 0.f};
@@ -292,263 +377,336 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
 #pragma unroll
                 for (int o = kCGL / 2; o > 0; o >>= 1) { at.x += shfl_x(at.x, o); at.y += shfl_x(at.y, o); }
             }
-            sc<float> prod{1.f, 0.f, 0}, pp{1.f, 0.f, 0};
-            bool big = false;
-            float *qf = reinterpret_cast<float *>(qc + (size_t)tl * RF4);
             const cx<float> *br = md.bvec + (size_t)r * M;
+            bool big = false;
+            float *cf = reinterpret_cast<float *>(cc + (size_t)rl * RF4);
 #pragma unroll
-            for (int j = 0; j < MPL; ++j) {
-                const int m = gl + kCGL * j;
-                cx<float> q{0.f, 0.f};
-                if (m < M) {
-                    cx<float> th{sign * thp[j].x, sign * thp[j].y};
-                    if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
-                    cx<float> mant, pv;
-                    int k;
-                    cosh2(th, mant, k, pv);
-                    const cx<float> c = cmul(mk(prod.x, prod.y), mant);
-                    prod = sc_norm(sc<float>{c.x, c.y, prod.e + k});
-                    pp = sc_mul(pp, sc<float>{pv.x, pv.y, 0});
-                    const float d = pv.x * pv.x + pv.y * pv.y;
-                    if (d > 0.f) {
-                        const float id = 1.f / d;
-                        q = cx<float>{pv.x * id - 1.f, -pv.y * id};
-                    } else {
-                        q = cx<float>{0x1p60f, 0.f};   // p = 0 (the unit's factor is 1 - p: q is not used)
+            for (int sg = 0; sg < NS; ++sg) {
+                const float sign = sg ? -1.f : 1.f;
+                sc<float> prod{1.f, 0.f, 0}, pp{1.f, 0.f, 0};
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    const int m = gl + kCGL * j;
+                    cx<float> c{0.f, 0.f};
+                    if (m < M) {
+                        // theta' = -(x + b) for sigma = +1, -x + b for sigma = -1
+                        cx<float> th{-xs[j].x, -xs[j].y};
+                        if (md.use_bias) { const cx<float> b = br[m]; th.x -= sign * b.x; th.y -= sign * b.y; }
+                        cx<float> mant, pv;
+                        int k;
+                        cosh2(th, mant, k, pv);
+                        const cx<float> z = cmul(mk(prod.x, prod.y), mant);
+                        prod = sc_norm(sc<float>{z.x, z.y, prod.e + k});
+                        pp = sc_mul(pp, sc<float>{pv.x, pv.y, 0});
+                        const float d = pv.x * pv.x + pv.y * pv.y;
+                        if (d > 0.f) {
+                            const float id = 1.f / d;
+                            c = cx<float>{pv.x * id - 1.f, -pv.y * id};
+                        } else {
+                            c = cx<float>{0x1p60f, 0.f};   // p(theta') = 0 (the unit's factor does not use c)
+                        }
+                        big = big || !(c.x * c.x + c.y * c.y <= 0x1p24f);
                     }
-                    big = big || !(q.x * q.x + q.y * q.y <= 0x1p24f);
+                    if (sg == 0) {   // the row keeps c of sign +1 only: c(-1) = c(+1) e^{-4b}
+                        int ore, oim;
+                        row_offsets<MPL>(j, gl, ore, oim);
+                        if (active) { cf[ore] = c.x; cf[oim] = c.y; }
+                    }
                 }
-                int ore, oim;
-                row_offsets<MPL>(j, gl, ore, oim);
-                if (active) { qf[ore] = q.x; qf[oim] = q.y; }
+                prod = group_prod<kCGL>(prod);
+                pp = group_prod<kCGL>(pp);
+                if (gl == 0 && active) {
+                    const cx<float> lc = md.logc[r];
+                    sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
+                    float ch = md.chi[g];
+                    if (sg && md.chiP < 0) ch = -ch;
+                    lead.x *= ch; lead.y *= ch;
+                    const sc<float> tm = sc_mul(prod, sc_norm(lead));
+                    tcb[rl * NS + sg] = sc_mul(tm, pp);
+                    so = sc_add(so, tm);
+                }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, big);
-            prod = group_prod<kCGL>(prod);
-            pp = group_prod<kCGL>(pp);
-            if (gl == 0 && active) {
-                const cx<float> lc = md.logc[r];
-                sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
-                float c = md.chi[g];
-                if (sign < 0 && md.chiP < 0) c = -c;
-                lead.x *= c; lead.y *= c;
-                const sc<float> tm = sc_mul(prod, sc_norm(lead));
-                term[tl] = tm;
-                tpr[tl] = sc_mul(tm, pp);
-                bigf[tl] = ((bal >> gbase) & 0xffu) != 0;
-            }
+            if (gl == 0 && active) bigf[rl] = ((bal >> gbase) & 0xffu) != 0;
+        }
+        {
+            const sc<float> t = cluster_sum(so, wsum, xch + (size_t)(gstep & 1) * CL * 4, CL, rank);
+            ++gstep;
+            if (threadIdx.x == 0) s_cur = t;
         }
         __syncthreads();
 
         const int total = n_burn + n_per_chain * n_skip;
         int n_acc = 0;
-        if (threadIdx.x == 0) {
-            const u32x4 w = philox(0u, 0u, 0u, 0u, k0, k1);
-            site_u = kth_set(upm, md.nwords, (int)(((uint64_t)w.v[0] * (uint64_t)(N / 2)) >> 32));
-            site_d = kth_set(dnm, md.nwords, (int)(((uint64_t)w.v[1] * (uint64_t)(N / 2)) >> 32));
-            u_sh = (float)(w.v[2] >> 8) * (1.0f / 16777216.0f);
-            pend = 0; pend_u = 0; pend_d = 0;   // no exchange to apply before the first step
-        }
-        __syncthreads();
         for (int step = 0; step < total; ++step, ++gstep) {
-            const int iu = site_u, id = site_d;
-            // the previous step's exchange, if accepted, is applied to q in this pass
-            const int pending = pend, pu = pend_u, pd = pend_d;
+            // this step's proposal: the candidate for the previous step's outcome
+            const int pending = pend;   // the previous step's exchange was accepted: apply it to c in this pass
+            const int iu = pending ? cand[2] : cand[0], id = pending ? cand[3] : cand[1];
+            const int pu = pend_u, pd = pend_d;
+            const sc<float> *tcur = tcb + tsel * TP;
+            sc<float> *tnxt = tcb + (tsel ^ 1) * TP;
             if (threadIdx.x == 32 && step + 1 < total) {
                 // the next step's Philox words, ahead of this step's decision
                 const u32x4 w = philox((uint32_t)(step + 1), 0u, 0u, 0u, k0, k1);
-                wnext[0] = w.v[0]; wnext[1] = w.v[1]; wnext[2] = w.v[2];
+                uint32_t *wn = wnx[(step + 1) & 1];
+                wn[0] = w.v[0]; wn[1] = w.v[1]; wn[2] = w.v[2];
             }
-            // ---- one pass: q <- q / U' for a pending exchange (U' its factors),
-            //      then prod_m (q_m + U_m) of this proposal per pair ----
-            for (int tb = 0; tb < ntp; tb += nslots) {
-                const int tl0 = tb + slot;
-                const bool active = tl0 < ntp;
-                const int tl = active ? tl0 : 0;
-                const int t = t0 + tl;
-                const int row = md.nsign == 2 ? t >> 1 : t;
-                const int sg = t - row * md.nsign;
-                const int r = md.K == 1 ? 0 : row / md.G, g = row - r * md.G;
-                const uint8_t *pg = md.perm + (size_t)g * N;
-                const int rs = r * 2 * N;
-                const float4 *Su = s4 + (size_t)(rs + sg * N + pg[iu]) * RF4 + gl;          // exp(-4 sigma W_u)
-                const float4 *Sd = s4 + (size_t)(rs + (sg ^ 1) * N + pg[id]) * RF4 + gl;    // exp(+4 sigma W_d)
-                // 1/U' of the pending exchange: the factors of the opposite orientation
-                const float4 *Vu = s4 + (size_t)(rs + (sg ^ 1) * N + pg[pu]) * RF4 + gl;
-                const float4 *Vd = s4 + (size_t)(rs + sg * N + pg[pd]) * RF4 + gl;
-                float4 *qr = qc + (size_t)tl * RF4 + gl;
-                bool big = bigf[tl] != 0;
-                f2 Rx = 0, Ry = 0;
-                int elo = 0, ehi = 0;
+            // ---- one pass per row: c <- c U' for a pending exchange (U' its
+            //      factors) and prod_m (1 + c_m U_m) of this proposal for each
+            //      sign; then per pair the new term and tc after an acceptance ----
+            sc<float> sn{0.f, 0.f, 0};
+            // The rows of a group come in chunks of CH: the chunk's 8 pairs
+            // k = it NS + sg have their lane products combined by a
+            // reduce-scatter over the group's 8 lanes (levels xor 4, 2, 1), after
+            // which lane gl holds pair k = 4 bit0(gl) + 2 bit1(gl) + bit2(gl)
+            // and computes that pair's new term.
+            constexpr int CH = 8 / NS;
+            const int my_k = ((gl & 1) << 2) | (gl & 2) | ((gl >> 2) & 1);
+            const int my_it = my_k / NS, my_sg = my_k % NS;
+            for (int tb = 0; tb < ntr; tb += CH * nslots) {
+                float h0x = 1.f, h0y = 0.f, h1x = 1.f, h1y = 0.f, h2x = 1.f, h2y = 0.f;
+                int h0e = 0, h1e = 0, h2e = 0;
+                float fx = 1.f, fy = 0.f;   // the lane's pair after the last level
+                int fe = 0;
+#pragma unroll 1
+                for (int it = 0; it < CH; ++it) {
+                    const int rl0 = tb + it * nslots + slot;
+                    const bool active = rl0 < ntr;
+                    float x[NS], y[NS];
+                    int ex[NS];
 #pragma unroll
-                for (int i = 0; i < NPAIR; ++i) {
-                    f2 qx, qy;
-                    lds128(qr + 8 * i, qx, qy);
-                    if (pending) {
-                        f2 ax, ay, bx, by;
-                        lds128(Vu + 8 * i, ax, ay);
-                        lds128(Vd + 8 * i, bx, by);
-                        const f2 vx = sub2(mul2(ax, bx), mul2(ay, by)), vy = fma2(ax, by, mul2(ay, bx));
-                        const f2 nx = sub2(mul2(qx, vx), mul2(qy, vy));
-                        qy = fma2(qx, vy, mul2(qy, vx));
-                        qx = nx;
-                        if (active) sts128(qr + 8 * i, qx, qy);
-                        const f2 qq = fma2(qx, qx, mul2(qy, qy));
-                        big = big || !(f2_lo(qq) <= 0x1p24f) || !(f2_hi(qq) <= 0x1p24f);
-                    }
-                    f2 ux, uy, dx, dy;
-                    lds128(Su + 8 * i, ux, uy);
-                    lds128(Sd + 8 * i, dx, dy);
-                    const f2 wx = sub2(fma2(ux, dx, qx), mul2(uy, dy));   // q + U
-                    const f2 wy = fma2(ux, dy, fma2(uy, dx, qy));
-                    if (i == 0) {
-                        Rx = wx; Ry = wy;
-                    } else {
-                        const f2 nx = sub2(mul2(Rx, wx), mul2(Ry, wy));
-                        Ry = fma2(Rx, wy, mul2(Ry, wx));
-                        Rx = nx;
-                    }
-                    if (big) {   // renormalise the even and the odd units' products
-                        float xl = f2_lo(Rx), yl = f2_lo(Ry), xh = f2_hi(Rx), yh = f2_hi(Ry);
-                        elo += nrm(xl, yl);
-                        ehi += nrm(xh, yh);
-                        Rx = f2_pack(xl, xh);
-                        Ry = f2_pack(yl, yh);
-                    }
-                }
-                float x, y;
-                int ex;
-                {
-                    float xl = f2_lo(Rx), yl = f2_lo(Ry), xh = f2_hi(Rx), yh = f2_hi(Ry);
-                    elo += nrm(xl, yl);
-                    ehi += nrm(xh, yh);
-                    x = xl * xh - yl * yh;
-                    y = xl * yh + yl * xh;
-                    ex = elo + ehi;
-                }
-                if (SGL) {
-                    const int o2 = (MPL - 1) * 8;   // float2 index of lane 0's single unit
-                    float2 *qs = reinterpret_cast<float2 *>(qc + (size_t)tl * RF4) + o2 + gl;
-                    float qx = qs->x, qy = qs->y;
-                    if (pending) {
-                        float ax, ay, bx, by;
-                        lds64(reinterpret_cast<const float2 *>(Vu - gl) + o2 + gl, ax, ay);
-                        lds64(reinterpret_cast<const float2 *>(Vd - gl) + o2 + gl, bx, by);
-                        const float vx = ax * bx - ay * by, vy = ax * by + ay * bx;
-                        const float nx = qx * vx - qy * vy;
-                        qy = qx * vy + qy * vx;
-                        qx = nx;
-                        if (active) *qs = make_float2(qx, qy);
-                        big = big || !(qx * qx + qy * qy <= 0x1p24f);
-                    }
-                    float ux, uy, dx, dy;
-                    lds64(reinterpret_cast<const float2 *>(Su - gl) + o2 + gl, ux, uy);
-                    lds64(reinterpret_cast<const float2 *>(Sd - gl) + o2 + gl, dx, dy);
-                    const float wx = qx + ux * dx - uy * dy, wy = qy + ux * dy + uy * dx;
-                    const float nx = x * wx - y * wy;
-                    y = x * wy + y * wx;
-                    x = nx;
-                }
-                ex += nrm(x, y);
-                const unsigned bal = __ballot_sync(0xffffffffu, big);
-                // product over the group's 8 lanes: the mantissas are in [1, 2), so
-                // the product's stays below 2^8 with no renormalisation (the term
-                // pass normalises it)
+                    for (int sg = 0; sg < NS; ++sg) { x[sg] = 1.f; y[sg] = 0.f; ex[sg] = 0; }
+                    if (tb + it * nslots < ntr) {   // some group of the CTA has a row
+                        const int rl = active ? rl0 : 0;
+                        const int row = r0 + rl;
+                        const int r = md.K == 1 ? 0 : row / md.G, g = row - r * md.G;
+                        const uint8_t *pg = md.perm + (size_t)g * N;
+                        const int rs = r * 2 * N;
+                        const int ku = pg[iu], kd = pg[id];
+                        // shared-memory addresses of the lane's first float4 in the rows
+                        const uint32_t Su = a_s4 + (uint32_t)(((rs + ku) * RF4 + gl) * 16);         // exp(-4 W_u)
+                        const uint32_t Sd = a_s4 + (uint32_t)(((rs + N + kd) * RF4 + gl) * 16);     // exp(+4 W_d)
+                        const uint32_t Vu = a_s4 + (uint32_t)(((rs + pg[pu]) * RF4 + gl) * 16);     // the same for the
+                        const uint32_t Vd = a_s4 + (uint32_t)(((rs + N + pg[pd]) * RF4 + gl) * 16); // pending exchange
+                        const uint32_t Br = a_bt + (uint32_t)((r * RF4 + gl) * 16);
+                        const uint32_t cr = a_cc + (uint32_t)((rl * RF4 + gl) * 16);
+                        // float2 offset from a lane's first float4 to its single unit
+                        constexpr uint32_t o2b = (uint32_t)((MPL - 1) * 8 * 8);
+                        const uint32_t o2 = o2b - (uint32_t)(gl * 8);
+                        if (BREG && r != rcur) {
+                            rcur = r;
 #pragma unroll
-                for (int o = kCGL / 2; o > 0; o >>= 1) {
-                    const float ox = shfl_x(x, o), oy = shfl_x(y, o);
-                    const int oe = __shfl_xor_sync(0xffffffffu, ex, o);
-                    const float nx = x * ox - y * oy;
-                    y = x * oy + y * ox;
-                    x = nx;
-                    ex += oe;
+                            for (int i = 0; i < NPAIR; ++i) lds128(Br + 128 * i, bx[i], by[i]);
+                            if (SGL) lds64(Br + o2, bsx, bsy);
+                        }
+                        const bool big = bigf[rl] != 0;
+                        float cm = 0.f;   // max_m |c_m|^2 after a pending update
+                        f2 Rx[NS], Ry[NS];
+                        int elo[NS], ehi[NS];
+#pragma unroll
+                        for (int sg = 0; sg < NS; ++sg) { elo[sg] = 0; ehi[sg] = 0; }
+#pragma unroll
+                        for (int i = 0; i < NPAIR; ++i) {
+                            f2 ux, uy, dx, dy;
+                            lds128(Su + 128 * i, ux, uy);
+                            lds128(Sd + 128 * i, dx, dy);
+                            const f2 Ux = sub2(mul2(ux, dx), mul2(uy, dy)), Uy = fma2(ux, dy, mul2(uy, dx));
+                            const f2 nUy = mul2(Uy, mone2);
+                            f2 cx0, cy0;
+                            lds128(cr + 128 * i, cx0, cy0);
+                            if (pending) {
+                                f2 ax, ay, vx, vy;
+                                lds128(Vu + 128 * i, ax, ay);
+                                lds128(Vd + 128 * i, vx, vy);
+                                const f2 Vx = sub2(mul2(ax, vx), mul2(ay, vy)), Vy = fma2(ax, vy, mul2(ay, vx));
+                                const f2 nx = sub2(mul2(cx0, Vx), mul2(cy0, Vy));
+                                cy0 = fma2(cx0, Vy, mul2(cy0, Vx));
+                                cx0 = nx;
+                                if (active) sts128(cr + 128 * i, cx0, cy0);
+                                const f2 cq = fma2(cx0, cx0, mul2(cy0, cy0));
+                                cm = fmaxf(cm, fmaxf(f2_lo(cq), f2_hi(cq)));
+                            }
+#pragma unroll
+                            for (int sg = 0; sg < NS; ++sg) {
+                                f2 cxs = cx0, cys = cy0;
+                                if (sg) {   // c of sign -1 = c e^{-4b}
+                                    f2 b_x, b_y;
+                                    if (BREG) { b_x = bx[i]; b_y = by[i]; }
+                                    else lds128(Br + 128 * i, b_x, b_y);
+                                    cxs = sub2(mul2(cx0, b_x), mul2(cy0, b_y));
+                                    cys = fma2(cx0, b_y, mul2(cy0, b_x));
+                                }
+                                const f2 wx = fma2(cys, nUy, fma2(cxs, Ux, one2));   // 1 + c U
+                                const f2 wy = fma2(cxs, Uy, mul2(cys, Ux));
+                                if (i == 0) {
+                                    Rx[sg] = wx; Ry[sg] = wy;
+                                } else {
+                                    const f2 nx = sub2(mul2(Rx[sg], wx), mul2(Ry[sg], wy));
+                                    Ry[sg] = fma2(Rx[sg], wy, mul2(Ry[sg], wx));
+                                    Rx[sg] = nx;
+                                }
+                                if (big) {   // renormalise the even and the odd units' products
+                                    float xl = f2_lo(Rx[sg]), yl = f2_lo(Ry[sg]), xh = f2_hi(Rx[sg]), yh = f2_hi(Ry[sg]);
+                                    elo[sg] += nrm(xl, yl);
+                                    ehi[sg] += nrm(xh, yh);
+                                    Rx[sg] = f2_pack(xl, xh);
+                                    Ry[sg] = f2_pack(yl, yh);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int sg = 0; sg < NS; ++sg) {
+                            float xl = f2_lo(Rx[sg]), yl = f2_lo(Ry[sg]), xh = f2_hi(Rx[sg]), yh = f2_hi(Ry[sg]);
+                            elo[sg] += nrm(xl, yl);
+                            ehi[sg] += nrm(xh, yh);
+                            x[sg] = xl * xh - yl * yh;
+                            y[sg] = xl * yh + yl * xh;
+                            ex[sg] = elo[sg] + ehi[sg];
+                        }
+                        if (SGL) {
+                            float ux, uy, dx, dy;
+                            lds64(Su + o2, ux, uy);
+                            lds64(Sd + o2, dx, dy);
+                            const float Ux = ux * dx - uy * dy, Uy = ux * dy + uy * dx;
+                            float c0x, c0y;
+                            lds64(cr + o2, c0x, c0y);
+                            if (pending) {
+                                float ax, ay, vx, vy;
+                                lds64(Vu + o2, ax, ay);
+                                lds64(Vd + o2, vx, vy);
+                                const float Vx = ax * vx - ay * vy, Vy = ax * vy + ay * vx;
+                                const float nx = c0x * Vx - c0y * Vy;
+                                c0y = c0x * Vy + c0y * Vx;
+                                c0x = nx;
+                                if (active) sts64(cr + o2, c0x, c0y);
+                                cm = fmaxf(cm, c0x * c0x + c0y * c0y);
+                            }
+#pragma unroll
+                            for (int sg = 0; sg < NS; ++sg) {
+                                float cxs = c0x, cys = c0y;
+                                if (sg) {
+                                    float b_x = bsx, b_y = bsy;
+                                    if (!BREG) lds64(Br + o2, b_x, b_y);
+                                    cxs = c0x * b_x - c0y * b_y;
+                                    cys = c0x * b_y + c0y * b_x;
+                                }
+                                const float wx = 1.f + cxs * Ux - cys * Uy, wy = cxs * Uy + cys * Ux;
+                                const float nx = x[sg] * wx - y[sg] * wy;
+                                y[sg] = x[sg] * wy + y[sg] * wx;
+                                x[sg] = nx;
+                            }
+                        }
+#pragma unroll
+                        for (int sg = 0; sg < NS; ++sg) ex[sg] += nrm(x[sg], y[sg]);
+                        const unsigned bal = __ballot_sync(0xffffffffu, !(cm <= c0lim));
+                        if (gl == 0 && active && ((bal >> gbase) & 0xffu)) bigf[rl] = 1;
+                    }
+                    // reduce-scatter step for the pairs k = it NS + sg; the lane
+                    // mantissas are in [1, 2), so no product of at most 8 of them
+                    // needs renormalising
+#pragma unroll
+                    for (int sg = 0; sg < NS; ++sg) {
+                        const int k = it * NS + sg;
+                        if ((k & 1) == 0) { h0x = x[sg]; h0y = y[sg]; h0e = ex[sg]; continue; }
+                        const bool b2 = (gl >> 2) & 1;   // keeps the odd pair
+                        float kx = b2 ? x[sg] : h0x, ky = b2 ? y[sg] : h0y;
+                        int ke = b2 ? ex[sg] : h0e;
+                        float sx = b2 ? h0x : x[sg], sy = b2 ? h0y : y[sg];
+                        int se = b2 ? h0e : ex[sg];
+                        float ox = shfl_x(sx, 4), oy = shfl_x(sy, 4);
+                        int oe = __shfl_xor_sync(0xffffffffu, se, 4);
+                        float vx = kx * ox - ky * oy, vy = kx * oy + ky * ox;
+                        int ve = ke + oe;
+                        if (((k >> 1) & 1) == 0) { h1x = vx; h1y = vy; h1e = ve; continue; }
+                        const bool b1 = (gl >> 1) & 1;
+                        kx = b1 ? vx : h1x; ky = b1 ? vy : h1y; ke = b1 ? ve : h1e;
+                        sx = b1 ? h1x : vx; sy = b1 ? h1y : vy; se = b1 ? h1e : ve;
+                        ox = shfl_x(sx, 2); oy = shfl_x(sy, 2);
+                        oe = __shfl_xor_sync(0xffffffffu, se, 2);
+                        vx = kx * ox - ky * oy; vy = kx * oy + ky * ox;
+                        ve = ke + oe;
+                        if (((k >> 2) & 1) == 0) { h2x = vx; h2y = vy; h2e = ve; continue; }
+                        const bool b0 = gl & 1;
+                        kx = b0 ? vx : h2x; ky = b0 ? vy : h2y; ke = b0 ? ve : h2e;
+                        sx = b0 ? h2x : vx; sy = b0 ? h2y : vy; se = b0 ? h2e : ve;
+                        ox = shfl_x(sx, 1); oy = shfl_x(sy, 1);
+                        oe = __shfl_xor_sync(0xffffffffu, se, 1);
+                        fx = kx * ox - ky * oy; fy = kx * oy + ky * ox;
+                        fe = ke + oe;
+                    }
                 }
-                const sc<float> gq{x, y, ex};
-                if (gl == 0 && active) {
-                    if (pending) { term[tl] = nterm[tl]; tpr[tl] = ntpr[tl]; }
-                    if ((bal >> gbase) & 0xffu) bigf[tl] = 1;
-                    nterm[tl] = gq;   // prod_m (q_m + U_m) of this proposal, for the term pass
+                // the lane's pair: new term tc x prefactor x prod_m (1 + c_m U_m) x X
+                // and tc after an acceptance, tc x prefactor x X
+                const int m_rl = tb + my_it * nslots + slot;
+                if (m_rl < ntr) {
+                    const int row = r0 + m_rl;
+                    const int r = md.K == 1 ? 0 : row / md.G, g = row - r * md.G;
+                    const int m_ku = md.perm[(size_t)g * N + iu], m_kd = md.perm[(size_t)g * N + id];
+                    const int sg = my_sg, tp = m_rl * NS + sg, rs = r * 2 * N;
+                    const sc<float> tc = tcur[tp];
+                    const sc<float> a = es[rs + sg * N + m_ku], b = es[rs + (sg ^ 1) * N + m_kd];
+                    cx<float> base = cmul(cmul(mk(tc.x, tc.y), mk(a.x, a.y)), mk(b.x, b.y));
+                    int eb = tc.e + a.e + b.e;
+                    if (sg) {   // X = prod_m 1/U_m
+                        const sc<float> ca = ec[rs + N + m_ku], cb = ec[rs + m_kd];
+                        base = cmul(base, cmul(mk(ca.x, ca.y), mk(cb.x, cb.y)));
+                        eb += ca.e + cb.e;
+                    }
+                    eb += nrm(base.x, base.y);
+                    cx<float> mn = cmul(base, mk(fx, fy));
+                    const int en = eb + fe + nrm(mn.x, mn.y);
+                    tnxt[tp] = sc<float>{base.x, base.y, eb};
+                    sn = sc_add(sn, sc<float>{mn.x, mn.y, en});
                 }
             }
-            __syncthreads();
-            // ---- new terms: term x prod_m p_m x prod_m (q_m + U_m) x prefactor;
-            //      this CTA's sums of old and new terms ----
-            sc<float> so{0.f, 0.f, 0}, sn{0.f, 0.f, 0};
-            for (int tl = threadIdx.x; tl < ntp; tl += blockDim.x) {
-                const int t = t0 + tl;
-                const int row = md.nsign == 2 ? t >> 1 : t;
-                const int sg = t - row * md.nsign;
-                const int r = md.K == 1 ? 0 : row / md.G, g = row - r * md.G;
-                const int ku = md.perm[(size_t)g * N + iu], kd = md.perm[(size_t)g * N + id];
-                const int rs = r * 2 * N;
-                const sc<float> a = es[rs + sg * N + ku], b = es[rs + (sg ^ 1) * N + kd];
-                const sc<float> ca = ec[rs + sg * N + ku], cb = ec[rs + (sg ^ 1) * N + kd];
-                const sc<float> gq = nterm[tl], old = term[tl];
-                const sc<float> tp = tpr[tl];
-                const cx<float> pre = cmul(mk(a.x, a.y), mk(b.x, b.y));
-                // the new term, and term x prod p after acceptance (tpr x prefactor x prod_m U_m)
-                cx<float> mn = cmul(cmul(mk(tp.x, tp.y), mk(gq.x, gq.y)), pre);
-                const int en = tp.e + gq.e + a.e + b.e + nrm(mn.x, mn.y);
-                cx<float> mp = cmul(cmul(mk(tp.x, tp.y), pre), cmul(mk(ca.x, ca.y), mk(cb.x, cb.y)));
-                const int ep = tp.e + a.e + b.e + ca.e + cb.e + nrm(mp.x, mp.y);
-                const sc<float> tn{mn.x, mn.y, en};
-                nterm[tl] = tn;
-                ntpr[tl] = sc<float>{mp.x, mp.y, ep};
-                so = sc_add(so, old);
-                sn = sc_add(sn, tn);
-            }
-            // warp sums: scaled to the warp's largest exponent, then plain FP32
-            {
-                float v[4];
-                const int e = warp_scaled(so, sn, v);
-                if (lane == 0) { wold[warp] = sc<float>{v[0], v[1], e}; wnew[warp] = sc<float>{v[2], v[3], e}; }
-            }
-            __syncthreads();
-            float *slots = xch + (size_t)(gstep & 1) * CL * 8;
-            if (warp == 0) {
-                const sc<float> zero{0.f, 0.f, 0};
-                float v[4];
-                const int e = warp_scaled(lane < nwarps ? wold[lane] : zero, lane < nwarps ? wnew[lane] : zero, v);
-                const sc<float> a = sc_norm(sc<float>{v[0], v[1], e}), b = sc_norm(sc<float>{v[2], v[3], e});
-                // lanes q < CL send this CTA's sums to CTA q's slot [rank]
-                if (lane < CL) {
-                    const float x[6] = {a.x, a.y, __int_as_float(a.e), b.x, b.y, __int_as_float(b.e)};
-                    for (int k = 0; k < 6; ++k) st_cluster_f32(slots + rank * 8 + k, (uint32_t)lane, x[k]);
-                }
-            }
-            cluster_sync();
+            const sc<float> snew = cluster_sum(sn, wsum, xch + (size_t)(gstep & 1) * CL * 4, CL, rank);
+            const bool more = step + 1 < total;
             if (threadIdx.x == 0) {
-                // every CTA adds the partial sums in rank order: the same decision everywhere
-                sc<float> a{0.f, 0.f, 0}, b{0.f, 0.f, 0};
-                for (int q = 0; q < CL; ++q) {
-                    const float *sl = slots + q * 8;
-                    a = sc_add(a, sc<float>{sl[0], sl[1], __float_as_int(sl[2])});
-                    b = sc_add(b, sc<float>{sl[3], sl[4], __float_as_int(sl[5])});
-                }
                 // |new / old|^2 from the normalised mantissas (in [1, 2)) and the exponents
+                const sc<float> a = s_cur, b = snew;
                 const float q = (b.x * b.x + b.y * b.y) / (a.x * a.x + a.y * a.y);
                 const int de = 2 * (b.e - a.e);
-                const float r2 = de > 60 ? INFINITY : (de < -60 ? 0.f : ldexpf(q, de));
-                const int acc_now = u_sh < r2;
+                const float r2 = de > 60 ? INFINITY : (de < -60 ? 0.f : q * pow2i<float>(de));
+                const float u = (float)(wnx[step & 1][2] >> 8) * (1.0f / 16777216.0f);
+                const int acc_now = u < r2;
                 if (!isfinite(r2) && rank == 0) flag_range(md.status);
                 if (acc_now) {
-                    s_sm[iu] = -1.f; s_sm[id] = 1.f;
-                    upm[iu >> 6] &= ~(1ull << (iu & 63)); dnm[iu >> 6] |= 1ull << (iu & 63);
-                    dnm[id >> 6] &= ~(1ull << (id & 63)); upm[id >> 6] |= 1ull << (id & 63);
                     if (step >= n_burn) ++n_acc;
+                    s_cur = b;
+                    tsel ^= 1;
                 }
                 pend = acc_now; pend_u = iu; pend_d = id;
-                // the next proposal, in the configuration after this step
-                if (step + 1 < total) {
-                    site_u = kth_set(upm, md.nwords, (int)(((uint64_t)wnext[0] * (uint64_t)(N / 2)) >> 32));
-                    site_d = kth_set(dnm, md.nwords, (int)(((uint64_t)wnext[1] * (uint64_t)(N / 2)) >> 32));
-                    u_sh = (float)(wnext[2] >> 8) * (1.0f / 16777216.0f);
-                }
+            } else if (threadIdx.x == 32 && more) {
+                // the next proposal if this one is rejected: the configuration stays
+                const uint32_t *wn = wnx[(step + 1) & 1];
+                cand[0] = kth_set(upm, md.nwords, (int)(((uint64_t)wn[0] * (uint64_t)(N / 2)) >> 32));
+                cand[1] = kth_set(dnm, md.nwords, (int)(((uint64_t)wn[1] * (uint64_t)(N / 2)) >> 32));
+            } else if (threadIdx.x == 64 && more) {
+                // ... and if it is accepted: iu goes down, id goes up
+                uint64_t um[kMaxWords], dm[kMaxWords];
+                for (int q = 0; q < md.nwords; ++q) { um[q] = upm[q]; dm[q] = dnm[q]; }
+                um[iu >> 6] &= ~(1ull << (iu & 63)); dm[iu >> 6] |= 1ull << (iu & 63);
+                dm[id >> 6] &= ~(1ull << (id & 63)); um[id >> 6] |= 1ull << (id & 63);
+                const uint32_t *wn = wnx[(step + 1) & 1];
+                cand[2] = kth_set(um, md.nwords, (int)(((uint64_t)wn[0] * (uint64_t)(N / 2)) >> 32));
+                cand[3] = kth_set(dm, md.nwords, (int)(((uint64_t)wn[1] * (uint64_t)(N / 2)) >> 32));
             }
             __syncthreads();
-            // ---- keep every n_skip-th state after burn-in ----
-            if (rank == 0 && step >= n_burn && ((step - n_burn + 1) % n_skip) == 0 && threadIdx.x < md.nwords) {
-                const int kept = (step - n_burn + 1) / n_skip - 1;
-                cfg_out[((size_t)chain * n_per_chain + kept) * md.nwords + threadIdx.x] = upm[threadIdx.x];
+            // ---- the configuration after this step (one mask word per thread);
+            //      keep every n_skip-th state after burn-in ----
+            if (threadIdx.x < md.nwords) {
+                const int q = threadIdx.x;
+                uint64_t um = upm[q], dm = dnm[q];
+                if (pend) {
+                    if ((iu >> 6) == q) { um &= ~(1ull << (iu & 63)); dm |= 1ull << (iu & 63); }
+                    if ((id >> 6) == q) { dm &= ~(1ull << (id & 63)); um |= 1ull << (id & 63); }
+                    upm[q] = um; dnm[q] = dm;
+                    if (q == 0) { s_sm[iu] = -1.f; s_sm[id] = 1.f; }
+                }
+                if (rank == 0 && step >= n_burn && ((step - n_burn + 1) % n_skip) == 0) {
+                    const int kept = (step - n_burn + 1) / n_skip - 1;
+                    cfg_out[((size_t)chain * n_per_chain + kept) * md.nwords + q] = um;
+                }
             }
         }
         if (threadIdx.x == 0 && rank == 0 && acc_out)
@@ -580,10 +738,11 @@ bool launch_sample_cl(const DevModel<float> &md, uint64_t seed, int n_chains, in
     const ClPlan p = cl_plan(md, force);
     if (!p.CL) return false;
     void (*kern)(DevModel<float>, uint64_t, int, int, int, int, uint64_t *, float *, int, int) = nullptr;
-    if (need <= 2) kern = k_sample_cl<2>;
-    else if (need <= 4) kern = k_sample_cl<4>;
-    else if (need <= 9) kern = k_sample_cl<9>;
-    else kern = k_sample_cl<16>;
+    const bool two = md.nsign == 2;
+    if (need <= 2) kern = two ? k_sample_cl<2, 2> : k_sample_cl<2, 1>;
+    else if (need <= 4) kern = two ? k_sample_cl<4, 2> : k_sample_cl<4, 1>;
+    else if (need <= 9) kern = two ? k_sample_cl<9, 2> : k_sample_cl<9, 1>;
+    else kern = two ? k_sample_cl<16, 2> : k_sample_cl<16, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) { *err = e; return true; }
@@ -602,7 +761,7 @@ bool launch_sample_cl(const DevModel<float> &md, uint64_t seed, int n_chains, in
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, md, seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, p.CL, p.TP);
+    e = cudaLaunchKernelEx(&cfg, kern, md, seed, n_chains, n_per_chain, n_skip, n_burn, cfg_out, acc_out, p.CL, p.TR);
     *err = e == cudaSuccess ? cudaGetLastError() : e;
     return true;
 }
