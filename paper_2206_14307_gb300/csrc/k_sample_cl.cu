@@ -9,24 +9,30 @@
 //
 // Cache.  Per pair the chain keeps, per unit, c_m = e^{-2 theta'_m} with
 // theta' = -theta for sigma = +1 and theta' = theta for sigma = -1, and the
-// scalar tc = term x prod_m p(theta'_m), p(x) = e^x / (2 cosh x).  In this form
+// scalar tc = term x prod_m p(theta'_m), p(x) = e^x / (2 cosh x).  With
+// theta = sigma x + b, c(-1) = e^{2x - 2b} = c(+1) e^{-4b}: a row keeps c of
+// sign +1 only.  In this form
 // the unit factor of both signs is (1 + c_m U_m) -- for sigma = +1 it is
 // 1 + p(theta)(U - 1) = p(theta') (1 + c U), for sigma = -1 it is
 // p(theta')(1 + c U) / U -- so
 //   new term = tc x e^{sigma C_ud} x prod_m (1 + c_m U_m) x X,
 //   X = 1 (sigma = +1) or prod_m 1/U_m = e^{4 (CS_g(u) - CS_g(d))} (sigma = -1),
 // and an accepted exchange multiplies every c_m of both signs by U_m and tc by
-// e^{sigma C_ud} X.  The two signs of a row read the same site factors.
+// e^{sigma C_ud} X.  The two signs of a row read the same site factors.  The
+// pass stores c_m U_m in place, the cache after an acceptance; after a
+// rejection the next pass takes it back with 1/U_m, read from the site rows
+// of the opposite orientation.  tc keeps two buffers, the current one and the
+// one after an acceptance.
 //
 // Layout.  The rows of the chain are split over the CL CTAs of a cluster (one
 // CTA per SM); each CTA holds its rows' c, the per-site factors exp(-+4W) and
 // the per-pair scalars in shared memory.  A group of 8 lanes takes a row: one
-// pass reads the site factors of the proposal (and, after an acceptance, of
-// the accepted exchange, applied to c in place), forms prod_m (1 + c_m U_m) of
-// both signs and the row's new terms.  The CTA's sums of old and new terms go
-// to every CTA of the cluster through distributed shared memory; after one
+// pass reads the row's c and the site factors of the proposal (and, after a
+// rejection, those of the rejected exchange), forms prod_m (1 + c_m U_m) of
+// both signs and the row's new terms.  The CTA's sum of new terms goes to
+// every CTA of the cluster through distributed shared memory; after one
 // cluster barrier every CTA adds the CL partial sums in rank order and reaches
-// the same decision.
+// the same decision against the chain's sum of current terms.
 #include "common.cuh"
 #include "f2.cuh"
 #include "kernels.h"
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
             wnx[0][0] = w0.v[0]; wnx[0][1] = w0.v[1]; wnx[0][2] = w0.v[2];
             cand[0] = kth_set(upm, md.nwords, (int)(((uint64_t)w0.v[0] * (uint64_t)(N / 2)) >> 32));
             cand[1] = kth_set(dnm, md.nwords, (int)(((uint64_t)w0.v[1] * (uint64_t)(N / 2)) >> 32));
-            pend = 0; pend_u = 0; pend_d = 0;   // no exchange to apply before the first step
+            pend = 2; pend_u = 0; pend_d = 0;   // no previous step
             tsel = 0;
         }
         __syncthreads();
@@ -440,8 +446,10 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
         int n_acc = 0;
         for (int step = 0; step < total; ++step, ++gstep) {
             // this step's proposal: the candidate for the previous step's outcome
-            const int pending = pend;   // the previous step's exchange was accepted: apply it to c in this pass
-            const int iu = pending ? cand[2] : cand[0], id = pending ? cand[3] : cand[1];
+            // the c rows hold the values after an acceptance of the previous
+            // proposal; if it was rejected, this pass divides its factors out again
+            const bool undo = pend == 0;
+            const int iu = pend == 1 ? cand[2] : cand[0], id = pend == 1 ? cand[3] : cand[1];
             const int pu = pend_u, pd = pend_d;
             const sc<float> *tcur = tcb + tsel * TP;
             sc<float> *tnxt = tcb + (tsel ^ 1) * TP;
@@ -451,9 +459,10 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                 uint32_t *wn = wnx[(step + 1) & 1];
                 wn[0] = w.v[0]; wn[1] = w.v[1]; wn[2] = w.v[2];
             }
-            // ---- one pass per row: c <- c U' for a pending exchange (U' its
-            //      factors) and prod_m (1 + c_m U_m) of this proposal for each
-            //      sign; then per pair the new term and tc after an acceptance ----
+            // ---- one pass per row: c <- c / U' after a rejected exchange (U' its
+            //      factors), prod_m (1 + c_m U_m) of this proposal for each sign,
+            //      and c <- c U in place (the cache if it is accepted); then per
+            //      pair the new term and tc after an acceptance ----
             sc<float> sn{0.f, 0.f, 0};
             // The rows of a group come in chunks of CH: the chunk's 8 pairs
             // k = it NS + sg have their lane products combined by a
@@ -486,8 +495,8 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                         // shared-memory addresses of the lane's first float4 in the rows
                         const uint32_t Su = a_s4 + (uint32_t)(((rs + ku) * RF4 + gl) * 16);         // exp(-4 W_u)
                         const uint32_t Sd = a_s4 + (uint32_t)(((rs + N + kd) * RF4 + gl) * 16);     // exp(+4 W_d)
-                        const uint32_t Vu = a_s4 + (uint32_t)(((rs + pg[pu]) * RF4 + gl) * 16);     // the same for the
-                        const uint32_t Vd = a_s4 + (uint32_t)(((rs + N + pg[pd]) * RF4 + gl) * 16); // pending exchange
+                        const uint32_t Vu = a_s4 + (uint32_t)(((rs + N + pg[pu]) * RF4 + gl) * 16); // 1/U' of the
+                        const uint32_t Vd = a_s4 + (uint32_t)(((rs + pg[pd]) * RF4 + gl) * 16);     // rejected exchange
                         const uint32_t Br = a_bt + (uint32_t)((r * RF4 + gl) * 16);
                         const uint32_t cr = a_cc + (uint32_t)((rl * RF4 + gl) * 16);
                         // float2 offset from a lane's first float4 to its single unit
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                             if (SGL) lds64(Br + o2, bsx, bsy);
                         }
                         const bool big = bigf[rl] != 0;
-                        float cm = 0.f;   // max_m |c_m|^2 after a pending update
+                        float cm = 0.f;   // max_m |c_m U_m|^2
                         f2 Rx[NS], Ry[NS];
                         int elo[NS], ehi[NS];
 #pragma unroll
@@ -511,10 +520,9 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                             lds128(Su + 128 * i, ux, uy);
                             lds128(Sd + 128 * i, dx, dy);
                             const f2 Ux = sub2(mul2(ux, dx), mul2(uy, dy)), Uy = fma2(ux, dy, mul2(uy, dx));
-                            const f2 nUy = mul2(Uy, mone2);
                             f2 cx0, cy0;
                             lds128(cr + 128 * i, cx0, cy0);
-                            if (pending) {
+                            if (undo) {
                                 f2 ax, ay, vx, vy;
                                 lds128(Vu + 128 * i, ax, ay);
                                 lds128(Vd + 128 * i, vx, vy);
@@ -522,22 +530,27 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                                 const f2 nx = sub2(mul2(cx0, Vx), mul2(cy0, Vy));
                                 cy0 = fma2(cx0, Vy, mul2(cy0, Vx));
                                 cx0 = nx;
-                                if (active) sts128(cr + 128 * i, cx0, cy0);
-                                const f2 cq = fma2(cx0, cx0, mul2(cy0, cy0));
+                            }
+                            // c U: the cache after an acceptance, and the factor 1 + c U of sign +1
+                            const f2 qx = sub2(mul2(cx0, Ux), mul2(cy0, Uy)), qy = fma2(cx0, Uy, mul2(cy0, Ux));
+                            if (active) sts128(cr + 128 * i, qx, qy);
+                            {
+                                const f2 cq = fma2(qx, qx, mul2(qy, qy));
                                 cm = fmaxf(cm, fmaxf(f2_lo(cq), f2_hi(cq)));
                             }
 #pragma unroll
                             for (int sg = 0; sg < NS; ++sg) {
-                                f2 cxs = cx0, cys = cy0;
-                                if (sg) {   // c of sign -1 = c e^{-4b}
+                                f2 wx, wy;
+                                if (sg) {   // sign -1: 1 + c e^{-4b} U
                                     f2 b_x, b_y;
                                     if (BREG) { b_x = bx[i]; b_y = by[i]; }
                                     else lds128(Br + 128 * i, b_x, b_y);
-                                    cxs = sub2(mul2(cx0, b_x), mul2(cy0, b_y));
-                                    cys = fma2(cx0, b_y, mul2(cy0, b_x));
+                                    wx = fma2(b_y, mul2(qy, mone2), fma2(b_x, qx, one2));
+                                    wy = fma2(b_x, qy, mul2(b_y, qx));
+                                } else {
+                                    wx = add2(qx, one2);
+                                    wy = qy;
                                 }
-                                const f2 wx = fma2(cys, nUy, fma2(cxs, Ux, one2));   // 1 + c U
-                                const f2 wy = fma2(cxs, Uy, mul2(cys, Ux));
                                 if (i == 0) {
                                     Rx[sg] = wx; Ry[sg] = wy;
                                 } else {
@@ -570,7 +583,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                             const float Ux = ux * dx - uy * dy, Uy = ux * dy + uy * dx;
                             float c0x, c0y;
                             lds64(cr + o2, c0x, c0y);
-                            if (pending) {
+                            if (undo) {
                                 float ax, ay, vx, vy;
                                 lds64(Vu + o2, ax, ay);
                                 lds64(Vd + o2, vx, vy);
@@ -578,19 +591,19 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                                 const float nx = c0x * Vx - c0y * Vy;
                                 c0y = c0x * Vy + c0y * Vx;
                                 c0x = nx;
-                                if (active) sts64(cr + o2, c0x, c0y);
-                                cm = fmaxf(cm, c0x * c0x + c0y * c0y);
                             }
+                            const float qx = c0x * Ux - c0y * Uy, qy = c0x * Uy + c0y * Ux;
+                            if (active) sts64(cr + o2, qx, qy);
+                            cm = fmaxf(cm, qx * qx + qy * qy);
 #pragma unroll
                             for (int sg = 0; sg < NS; ++sg) {
-                                float cxs = c0x, cys = c0y;
+                                float wx = 1.f + qx, wy = qy;
                                 if (sg) {
                                     float b_x = bsx, b_y = bsy;
                                     if (!BREG) lds64(Br + o2, b_x, b_y);
-                                    cxs = c0x * b_x - c0y * b_y;
-                                    cys = c0x * b_y + c0y * b_x;
+                                    wx = 1.f + b_x * qx - b_y * qy;
+                                    wy = b_x * qy + b_y * qx;
                                 }
-                                const float wx = 1.f + cxs * Ux - cys * Uy, wy = cxs * Uy + cys * Ux;
                                 const float nx = x[sg] * wx - y[sg] * wy;
                                 y[sg] = x[sg] * wy + y[sg] * wx;
                                 x[sg] = nx;
@@ -675,7 +688,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                     s_cur = b;
                     tsel ^= 1;
                 }
-                pend = acc_now; pend_u = iu; pend_d = id;
+                pend = acc_now; pend_u = iu; pend_d = id;   // 1 accepted, 0 rejected
             } else if (threadIdx.x == 32 && more) {
                 // the next proposal if this one is rejected: the configuration stays
                 const uint32_t *wn = wnx[(step + 1) & 1];
@@ -697,7 +710,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
             if (threadIdx.x < md.nwords) {
                 const int q = threadIdx.x;
                 uint64_t um = upm[q], dm = dnm[q];
-                if (pend) {
+                if (pend == 1) {
                     if ((iu >> 6) == q) { um &= ~(1ull << (iu & 63)); dm |= 1ull << (iu & 63); }
                     if ((id >> 6) == q) { dm &= ~(1ull << (id & 63)); um |= 1ull << (id & 63); }
                     upm[q] = um; dnm[q] = dm;
