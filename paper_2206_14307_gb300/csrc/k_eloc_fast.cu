@@ -52,13 +52,16 @@ struct EfArgs {
 // Im p, -Im p).
 template <int NP, bool QF>
 __device__ __forceinline__ void ef_entries(const DevModel<float> &md, const float4 *tps, const sc<float> *eps,
-                                           const uint16_t *aa, const uint16_t *bps, int naa, int r, int sg, int MH,
-                                           const f2 (&ca)[NP], const f2 (&cb)[NP], const f2 (&cc)[NP], int eref,
-                                           int gl, int gbase, float &accx, float &accy, double &Ox, double &Oy)
+                                           const uint16_t *aa, const uint16_t *bps, int naa, int ntrip, int r, int sg,
+                                           int MH, const f2 (&ca)[NP], const f2 (&cb)[NP], const f2 (&cc)[NP],
+                                           int eref, int gl, int gbase, float &accx, float &accy, double &Ox,
+                                           double &Oy)
 {
     const int NB = md.nbonds;
     const f2 one2 = f2_pack(1.f, 1.f);
-    for (int e0 = 0; e0 < naa; e0 += kEfGL) {
+    // ntrip >= naa is the same in every group of the warp (the shuffles below
+    // take all 32 lanes)
+    for (int e0 = 0; e0 < ntrip; e0 += kEfGL) {
         // lane gl: table offset and weighted prefactor of entry e0 + gl
         const int e = e0 + gl;
         int off = 0;
@@ -220,10 +223,17 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
 
         // (every group of a warp runs the same trip counts, so that the warp's
         // shuffles see all lanes; groups past the last row run row 0 and add
-        // nothing)
-        for (int rbase = 0; rbase < K * md.G; rbase += ngroups) {
-            const bool active = rbase + gidx < K * md.G;
-            const int row = active ? rbase + gidx : 0;
+        // nothing).  A last wave of at most ngroups / 2 (ngroups / 4) rows
+        // gives each row 2 (4) groups, each with its share of the entries.
+        for (int rbase = 0; rbase < K * md.G;) {
+            const int left = K * md.G - rbase;
+            const int split = 4 * left <= ngroups ? 4 : 2 * left <= ngroups ? 2 : 1;
+            const int part = gidx % split;
+            const bool active = rbase + gidx / split < K * md.G;
+            const int row = active ? rbase + gidx / split : 0;
+            const int e_lo = part * naa / split, e_n = (part + 1) * naa / split - e_lo;
+            const int e_max = (naa + split - 1) / split;   // the largest share: the same trip count in every group
+            rbase += ngroups / split;
             const int r = row / md.G, g = row - r * md.G;
             __syncwarp();
             for (int i = gl; i < N; i += kEfGL) pgs[i] = md.perm[(size_t)g * N + i];
@@ -312,7 +322,8 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
                 if (sg && md.chiP < 0) chg = -chg;
                 lead.x *= chg; lead.y *= chg;
                 const sc<float> wt = sc_mul(prod, sc_norm(lead));   // the row term (same in every lane)
-                if (gl == 0 && active) gsum[1][gidx] = sc_add(gsum[1][gidx], sc<double>{(double)wt.x, (double)wt.y, wt.e});
+                if (gl == 0 && active && part == 0)
+                    gsum[1][gidx] = sc_add(gsum[1][gidx], sc<double>{(double)wt.x, (double)wt.y, wt.e});
 
                 float accx = 0.f, accy = 0.f;
                 double Ox = 0.0, Oy = 0.0;
@@ -321,7 +332,7 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
                     const float u = f2_lo(Px) * f2_hi(Px) - f2_lo(Py) * f2_hi(Py);
                     const float v = f2_lo(Px) * f2_hi(Py) + f2_lo(Py) * f2_hi(Px);
                     const sc<float> Pp = group_prod<kEfGL>(sc<float>{u, v, 0});
-                    ef_entries<NP, true>(md, tps, eps, aa, bps, naa, r, sg, MH, ca, cb, cc, Pp.e, gl, gbase, accx, accy,
+                    ef_entries<NP, true>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, ca, cb, cc, Pp.e, gl, gbase, accx, accy,
                                          Ox, Oy);
                     mult = sc_mul(wt, sc<float>{Pp.x, Pp.y, 0});
                 } else {
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
                         cb[j] = f2_pack(pyv[0], pyv[1]);
                         cc[j] = f2_pack(-pyv[0], -pyv[1]);
                     }
-                    ef_entries<NP, false>(md, tps, eps, aa, bps, naa, r, sg, MH, ca, cb, cc, 0, gl, gbase, accx, accy,
+                    ef_entries<NP, false>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, ca, cb, cc, 0, gl, gbase, accx, accy,
                                           Ox, Oy);
                     mult = wt;
                 }
@@ -401,14 +412,16 @@ constexpr int kEpGL = 4;
 
 template <int NP, bool QF>
 __device__ __forceinline__ void ep_entries(const DevModel<float> &md, const float4 *tps, const sc<float> *eps,
-                                           const uint16_t *aa, const uint16_t *bps, int naa, int r, int sg, int MH,
-                                           int BS, const f2 (&ca)[NP], const f2 (&cb)[NP], const f2 (&cc)[NP],
-                                           int eref, int gl, int gbase, float &accx, float &accy, double &Ox,
-                                           double &Oy)
+                                           const uint16_t *aa, const uint16_t *bps, int naa, int ntrip, int r, int sg,
+                                           int MH, int BS, const f2 (&ca)[NP], const f2 (&cb)[NP],
+                                           const f2 (&cc)[NP], int eref, int gl, int gbase, float &accx, float &accy,
+                                           double &Ox, double &Oy)
 {
     const int NB = md.nbonds;
     const f2 one2 = f2_pack(1.f, 1.f);
-    for (int e0 = 0; e0 < naa; e0 += kEpGL) {
+    // ntrip >= naa is the same in every group of the warp (the shuffles below
+    // take all 32 lanes)
+    for (int e0 = 0; e0 < ntrip; e0 += kEpGL) {
         const int e = e0 + gl;
         int off = 0;
         sc<float> pre{0.f, 0.f, 0};
@@ -570,9 +583,17 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
         __syncthreads();
         const int naa = n_aa;
 
-        for (int rbase = 0; rbase < K * md.G; rbase += nrs) {
-            const bool active = rbase + rslot < K * md.G;
-            const int row = active ? rbase + rslot : 0;
+        // waves of nrs rows; a last wave of at most nrs / 2 (nrs / 4) rows
+        // gives each row 2 (4) slots, each with its share of the entries
+        for (int rbase = 0; rbase < K * md.G;) {
+            const int left = K * md.G - rbase;
+            const int split = 4 * left <= nrs ? 4 : 2 * left <= nrs ? 2 : 1;
+            const int part = rslot % split;
+            const bool active = rbase + rslot / split < K * md.G;
+            const int row = active ? rbase + rslot / split : 0;
+            const int e_lo = part * naa / split, e_n = (part + 1) * naa / split - e_lo;
+            const int e_max = (naa + split - 1) / split;   // the largest share: the same trip count in every group
+            rbase += nrs / split;
             const int r = K == 1 ? 0 : row / md.G, g = row - r * md.G;
             __syncwarp();
             for (int i = l8; i < N; i += 8) pgs[i] = md.perm[(size_t)g * N + i];
@@ -670,7 +691,8 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
             if (sg && md.chiP < 0) chg = -chg;
             lead.x *= chg; lead.y *= chg;
             const sc<float> wt = sc_mul(prod, sc_norm(lead));
-            if (gl == 0 && active) gsum[1][gslot] = sc_add(gsum[1][gslot], sc<double>{(double)wt.x, (double)wt.y, wt.e});
+            if (gl == 0 && active && part == 0)
+                gsum[1][gslot] = sc_add(gsum[1][gslot], sc<double>{(double)wt.x, (double)wt.y, wt.e});
 
             float accx = 0.f, accy = 0.f;
             double Ox = 0.0, Oy = 0.0;
@@ -679,7 +701,7 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
                 const float u = f2_lo(Px) * f2_hi(Px) - f2_lo(Py) * f2_hi(Py);
                 const float v = f2_lo(Px) * f2_hi(Py) + f2_lo(Py) * f2_hi(Px);
                 const sc<float> Pp = group_prod<kEpGL>(sc<float>{u, v, 0});
-                ep_entries<NP, true>(md, tps, eps, aa, bps, naa, r, sg, MH, BS, ca, cb, cc, Pp.e, gl, gbase, accx,
+                ep_entries<NP, true>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, BS, ca, cb, cc, Pp.e, gl, gbase, accx,
                                      accy, Ox, Oy);
                 mult = sc_mul(wt, sc<float>{Pp.x, Pp.y, 0});
             } else {
@@ -705,7 +727,7 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
                     cb[j] = f2_pack(pyv[0], pyv[1]);
                     cc[j] = f2_pack(-pyv[0], -pyv[1]);
                 }
-                ep_entries<NP, false>(md, tps, eps, aa, bps, naa, r, sg, MH, BS, ca, cb, cc, 0, gl, gbase, accx,
+                ep_entries<NP, false>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, BS, ca, cb, cc, 0, gl, gbase, accx,
                                       accy, Ox, Oy);
                 mult = wt;
             }
