@@ -75,10 +75,7 @@ __device__ __forceinline__ void ef_entries(const DevModel<float> &md, const floa
             const bool pos = ((code >> 15) != 0) != ((bp >> 15) != 0);   // s_i flip-corrected
             const int o = (pos != (sg != 0)) ? 0 : 1;
             off = ((r * 2 + o) * NB + bb) * MH;
-            pre = eps[(r * 2 + o) * NB + bb];
-            const float c1 = 0.5f * bondJ(md, b);
-            pre.x *= c1;
-            pre.y *= c1;
+            pre = eps[(r * 2 + o) * NB + bb];   // (J_b / 2) e^{+-C}
         }
         float rx[kEfGL], ry[kEfGL];
         int re[kEfGL];
@@ -409,6 +406,7 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
 // different bank halves.
 // ---------------------------------------------------------------------------
 constexpr int kEpGL = 4;
+constexpr int kEpQI = 2;   // entries whose running products interleave
 
 template <int NP, bool QF>
 __device__ __forceinline__ void ep_entries(const DevModel<float> &md, const float4 *tps, const sc<float> *eps,
@@ -419,6 +417,8 @@ __device__ __forceinline__ void ep_entries(const DevModel<float> &md, const floa
 {
     const int NB = md.nbonds;
     const f2 one2 = f2_pack(1.f, 1.f);
+    // shared-memory address of the lane's first float4 in table row 0
+    const uint32_t a_tps = (uint32_t)__cvta_generic_to_shared(tps) + (uint32_t)gl * 16u;
     // ntrip >= naa is the same in every group of the warp (the shuffles below
     // take all 32 lanes)
     for (int e0 = 0; e0 < ntrip; e0 += kEpGL) {
@@ -433,43 +433,49 @@ __device__ __forceinline__ void ep_entries(const DevModel<float> &md, const floa
             const bool pos = ((code >> 15) != 0) != ((bp >> 15) != 0);
             const int o = (pos != (sg != 0)) ? 0 : 1;
             off = (r * 2 + o) * BS + bb * MH;
-            pre = eps[(r * 2 + o) * NB + bb];
-            const float c1 = 0.5f * bondJ(md, b);
-            pre.x *= c1;
-            pre.y *= c1;
+            pre = eps[(r * 2 + o) * NB + bb];   // (J_b / 2) e^{+-C}
         }
         float rx[kEpGL], ry[kEpGL];
         int re[kEpGL];
+        // the group's entries kEpQI at a time side by side (independent running products)
+        uint32_t ta[kEpGL];
 #pragma unroll
-        for (int q = 0; q < kEpGL; ++q) {
-            const float4 *trow = tps + __shfl_sync(0xffffffffu, off, gbase + q) + gl;
-            f2 Rx = one2, Ry = 0;
+        for (int q = 0; q < kEpGL; ++q) ta[q] = a_tps + (uint32_t)__shfl_sync(0xffffffffu, off, gbase + q) * 16u;
+#pragma unroll
+        for (int q0 = 0; q0 < kEpGL; q0 += kEpQI) {
+            f2 Rx[kEpQI], Ry[kEpQI];
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                f2 ux, uy;
-                lds128(trow + kEpGL * j, ux, uy);
-                f2 fx, fy;
-                if constexpr (QF) {
-                    fx = add2(ux, ca[j]);
-                    fy = add2(uy, cb[j]);
-                } else {
-                    const f2 tx = sub2(ux, one2);
-                    fx = fma2(cc[j], uy, fma2(ca[j], tx, one2));
-                    fy = fma2(ca[j], uy, mul2(cb[j], tx));
-                }
-                if (j == 0) {
-                    Rx = fx; Ry = fy;
-                } else {
-                    const f2 nx = sub2(mul2(Rx, fx), mul2(Ry, fy));
-                    Ry = fma2(Rx, fy, mul2(Ry, fx));
-                    Rx = nx;
+#pragma unroll
+                for (int qi = 0; qi < kEpQI; ++qi) {
+                    f2 ux, uy;
+                    lds128(ta[q0 + qi] + 64u * j, ux, uy);
+                    f2 fx, fy;
+                    if constexpr (QF) {
+                        fx = add2(ux, ca[j]);
+                        fy = add2(uy, cb[j]);
+                    } else {
+                        const f2 tx = sub2(ux, one2);
+                        fx = fma2(cc[j], uy, fma2(ca[j], tx, one2));
+                        fy = fma2(ca[j], uy, mul2(cb[j], tx));
+                    }
+                    if (j == 0) {
+                        Rx[qi] = fx; Ry[qi] = fy;
+                    } else {
+                        const f2 nx = sub2(mul2(Rx[qi], fx), mul2(Ry[qi], fy));
+                        Ry[qi] = fma2(Rx[qi], fy, mul2(Ry[qi], fx));
+                        Rx[qi] = nx;
+                    }
                 }
             }
-            float x = f2_lo(Rx) * f2_hi(Rx) - f2_lo(Ry) * f2_hi(Ry);
-            float y = f2_lo(Rx) * f2_hi(Ry) + f2_lo(Ry) * f2_hi(Rx);
-            re[q] = nrm(x, y);
-            rx[q] = x;
-            ry[q] = y;
+#pragma unroll
+            for (int qi = 0; qi < kEpQI; ++qi) {
+                float x = f2_lo(Rx[qi]) * f2_hi(Rx[qi]) - f2_lo(Ry[qi]) * f2_hi(Ry[qi]);
+                float y = f2_lo(Rx[qi]) * f2_hi(Ry[qi]) + f2_lo(Ry[qi]) * f2_hi(Rx[qi]);
+                re[q0 + qi] = nrm(x, y);
+                rx[q0 + qi] = x;
+                ry[q0 + qi] = y;
+            }
         }
         // butterfly product-reduce-scatter over the group's 4 lanes
 #pragma unroll
@@ -768,7 +774,7 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
 
 // Paired tables from the connection tables of the model: tp[(r 2 + o) BS + b MH
 // + k] = (Ux_2k, Ux_2k+1, Uy_2k, Uy_2k+1), U = 1 + T, for unit pairs k < MH
-// (U = 1 past M), and ep = e^{(1 - 2 o) C_b} as scaled numbers.
+// (U = 1 past M), and ep = (J_b / 2) e^{(1 - 2 o) C_b} as scaled numbers.
 __global__ void k_tables_paired(DevModel<float> md, int MH, int BS, float4 *__restrict__ tp, sc<float> *__restrict__ ep)
 {
     const int NB = md.nbonds;
@@ -789,7 +795,9 @@ __global__ void k_tables_paired(DevModel<float> md, int MH, int BS, float4 *__re
         const int b = (int)(q - (int64_t)rb * NB);
         const int r = rb >> 1, o = rb & 1;
         const cx<float> c = md.Cb[(size_t)r * NB + b];
-        ep[q] = sc_norm(sc_exp(o ? cx<float>{-c.x, -c.y} : c));
+        const sc<float> v = sc_exp(o ? cx<float>{-c.x, -c.y} : c);
+        const float hj = 0.5f * bondJ(md, b);   // the symmetry images of a bond have its coupling
+        ep[q] = sc_norm(sc<float>{v.x * hj, v.y * hj, v.e});
     }
 }
 
