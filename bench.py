@@ -712,7 +712,8 @@ def main():
                    "precision": "BF16X2 theta GEMM on tensor cores for fresh amplitudes; FP32 with exact exponent tracking elsewhere", "l2": "flushed (512 MB write) before every step"},
         "eloc_samples_per_s": world * N_SAMPLES / (ms / 1e3),
         "acceptance": res["acc"], "E_loc_mean_per_site": res["e_mean"],
-        "roofline": {"kernel": "k_eloc_fast (E_loc with the per-bond tables in shared memory)", "bound": "alu",
+        "roofline": {"kernel": "k_eloc_pair (E_loc, the two signs of a row in one quarter-warp, per-bond tables "
+                               "in shared memory)", "bound": "alu",
                      "achieved": eloc_ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": eloc_ach / FP32_PEAK_TFLOPS, "traffic": K_RATIO_TRAFFIC,
                      "peak_source": f"FP32 FMA, {ALU_SOURCE}",
@@ -723,12 +724,13 @@ def main():
                        "fresh_amplitudes_per_s": N_SAMPLES / (res["ms_logpsi"] / 1e3),
                        "note": "algorithmic flop (4 K|G| M N per amplitude); the bf16 hi+lo split executes 2x; "
                                "the kernel is limited by its log-cosh epilogue, not the MMA"},
-        "sampler": {"kernel": "k_sample_cl (cluster sampler, each chain's cache in distributed shared memory)",
+        "sampler": {"kernel": "k_sample_cl (each chain's cache in the shared memory of one CTA, or of a "
+                              "cluster of CTAs for larger models; one CTA here)",
                     "bound": "latency",
                     "bound_note": "each Metropolis step of a chain is serial: the ratio pass over the chain's "
-                                  "cache, the exchange of partial sums over distributed shared memory, one "
-                                  "cluster barrier and the decision (ncu: short_scoreboard, wait and barrier "
-                                  "stalls); DRAM carries only the tables and the kept samples",
+                                  "cache, the CTA's sum, the decision and the next proposal (ncu: wait, "
+                                  "short_scoreboard and barrier stalls); DRAM carries only the tables and the "
+                                  "kept samples",
                     "achieved": samp_bytes / samp_s / 1e9, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
                     "frac": samp_bytes / samp_s / 1e9 / SMEM_PEAK_GBS,
                     "frac_kind": "algorithmic cache stream (8 K|G|M (1 + acceptance) B per proposal) read from "

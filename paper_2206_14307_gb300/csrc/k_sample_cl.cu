@@ -138,21 +138,26 @@ __device__ __forceinline__ sc<float> cluster_sum(sc<float> v, sc<float> *wsum, f
         if (lane == 0) wsum[warp] = sc<float>{w[0], w[1], e};
     }
     __syncthreads();
+    sc<float> t{0.f, 0.f, 0};
+    if (CL == 1) {   // one CTA: warp 0's sum is the total (thread 0 is in warp 0)
+        if (warp == 0) {
+            float w[2];
+            const int e = warp_scaled(lane < nwarps ? wsum[lane] : sc<float>{0.f, 0.f, 0}, w);
+            t = sc_norm(sc<float>{w[0], w[1], e});
+        }
+        return t;
+    }
     if (warp == 0) {
         float w[2];
         const int e = warp_scaled(lane < nwarps ? wsum[lane] : sc<float>{0.f, 0.f, 0}, w);
         const sc<float> a = sc_norm(sc<float>{w[0], w[1], e});
-        if (CL == 1) {
-            if (lane == 0) { slots[0] = a.x; slots[1] = a.y; slots[2] = __int_as_float(a.e); }
-        } else if (lane < CL) {   // lane q writes into CTA q's slot [rank]
+        if (lane < CL) {   // lane q writes into CTA q's slot [rank]
             st_cluster_f32(slots + rank * 4 + 0, (uint32_t)lane, a.x);
             st_cluster_f32(slots + rank * 4 + 1, (uint32_t)lane, a.y);
             st_cluster_f32(slots + rank * 4 + 2, (uint32_t)lane, __int_as_float(a.e));
         }
     }
-    if (CL > 1) cluster_sync();
-    else __syncthreads();
-    sc<float> t{0.f, 0.f, 0};
+    cluster_sync();
     if (threadIdx.x == 0)
         for (int q = 0; q < CL; ++q) t = sc_add(t, sc<float>{slots[q * 4], slots[q * 4 + 1], __float_as_int(slots[q * 4 + 2])});
     return t;
@@ -225,6 +230,131 @@ __device__ __forceinline__ void sts64(uint32_t addr, float x, float y)
     asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(x), "f"(y) : "memory");
 }
 
+// One row's pass for the lane's units: c <- c / U' after a rejection (UNDO),
+// c U stored in place, and the lane's share of prod_m (1 + c_m U_m) of each
+// sign as a mantissa (x, y) in [1, 2) and an exponent ex; cm = max_m |c_m U_m|^2.
+// BIG renormalises the even and the odd units' products after every unit pair
+// (rows where some |c| may exceed 2^12).  Addresses are shared-memory byte
+// addresses of the lane's first float4 in each row; o2 leads from there to the
+// lane's single unit (odd MPL).  bx, by (and bsx, -nbsy) hold Re e^{-4b} and
+// Im e^{-4b} of the lane's units when BREG.
+template <int MPL, int NS, bool BREG, bool UNDO, bool BIG>
+__device__ __forceinline__ void cl_row(uint32_t Su, uint32_t Sd, uint32_t Vu, uint32_t Vd, uint32_t Br, uint32_t cr,
+                                       uint32_t o2, bool active, const f2 *bx, const f2 *by, float bsx, float nbsy,
+                                       float (&x)[NS], float (&y)[NS], int (&ex)[NS], float &cm)
+{
+    constexpr int NPAIR = MPL / 2, SGL = MPL & 1;
+    const f2 one2 = f2_pack(1.f, 1.f);
+    f2 Rx[NS], Ry[NS];
+    int elo[NS], ehi[NS];
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) { elo[sg] = 0; ehi[sg] = 0; }
+#pragma unroll
+    for (int i = 0; i < NPAIR; ++i) {
+        f2 ux, uy, dx, dy;
+        lds128(Su + 128 * i, ux, uy);
+        lds128(Sd + 128 * i, dx, dy);
+        const f2 Ux = sub2(mul2(ux, dx), mul2(uy, dy)), Uy = fma2(ux, dy, mul2(uy, dx));
+        f2 cx0, cy0;
+        lds128(cr + 128 * i, cx0, cy0);
+        if (UNDO) {
+            f2 ax, ay, vx, vy;
+            lds128(Vu + 128 * i, ax, ay);
+            lds128(Vd + 128 * i, vx, vy);
+            const f2 Vx = sub2(mul2(ax, vx), mul2(ay, vy)), Vy = fma2(ax, vy, mul2(ay, vx));
+            const f2 nx = sub2(mul2(cx0, Vx), mul2(cy0, Vy));
+            cy0 = fma2(cx0, Vy, mul2(cy0, Vx));
+            cx0 = nx;
+        }
+        // c U: the cache after an acceptance, and the factor 1 + c U of sign +1
+        const f2 qx = sub2(mul2(cx0, Ux), mul2(cy0, Uy)), qy = fma2(cx0, Uy, mul2(cy0, Ux));
+        if (active) sts128(cr + 128 * i, qx, qy);
+        {
+            const f2 cq = fma2(qx, qx, mul2(qy, qy));
+            cm = fmaxf(cm, fmaxf(f2_lo(cq), f2_hi(cq)));
+        }
+#pragma unroll
+        for (int sg = 0; sg < NS; ++sg) {
+            f2 wx, wy;
+            if (sg) {   // sign -1: 1 + c e^{-4b} U
+                f2 b_x, b_y;
+                if (BREG) {
+                    b_x = bx[i]; b_y = by[i];
+                } else {
+                    lds128(Br + 128 * i, b_x, b_y);
+                }
+                wx = sub2(fma2(b_x, qx, one2), mul2(b_y, qy));
+                wy = fma2(b_x, qy, mul2(b_y, qx));
+            } else {
+                wx = add2(qx, one2);
+                wy = qy;
+            }
+            if (i == 0) {
+                Rx[sg] = wx; Ry[sg] = wy;
+            } else {
+                const f2 nx = sub2(mul2(Rx[sg], wx), mul2(Ry[sg], wy));
+                Ry[sg] = fma2(Rx[sg], wy, mul2(Ry[sg], wx));
+                Rx[sg] = nx;
+            }
+            if (BIG) {   // renormalise the even and the odd units' products
+                float xl = f2_lo(Rx[sg]), yl = f2_lo(Ry[sg]), xh = f2_hi(Rx[sg]), yh = f2_hi(Ry[sg]);
+                elo[sg] += nrm(xl, yl);
+                ehi[sg] += nrm(xh, yh);
+                Rx[sg] = f2_pack(xl, xh);
+                Ry[sg] = f2_pack(yl, yh);
+            }
+        }
+    }
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) {
+        float xl = f2_lo(Rx[sg]), yl = f2_lo(Ry[sg]), xh = f2_hi(Rx[sg]), yh = f2_hi(Ry[sg]);
+        elo[sg] += nrm(xl, yl);
+        ehi[sg] += nrm(xh, yh);
+        x[sg] = xl * xh - yl * yh;
+        y[sg] = xl * yh + yl * xh;
+        ex[sg] = elo[sg] + ehi[sg];
+    }
+    if (SGL) {
+        float ux, uy, dx, dy;
+        lds64(Su + o2, ux, uy);
+        lds64(Sd + o2, dx, dy);
+        const float Ux = ux * dx - uy * dy, Uy = ux * dy + uy * dx;
+        float c0x, c0y;
+        lds64(cr + o2, c0x, c0y);
+        if (UNDO) {
+            float ax, ay, vx, vy;
+            lds64(Vu + o2, ax, ay);
+            lds64(Vd + o2, vx, vy);
+            const float Vx = ax * vx - ay * vy, Vy = ax * vy + ay * vx;
+            const float nx = c0x * Vx - c0y * Vy;
+            c0y = c0x * Vy + c0y * Vx;
+            c0x = nx;
+        }
+        const float qx = c0x * Ux - c0y * Uy, qy = c0x * Uy + c0y * Ux;
+        if (active) sts64(cr + o2, qx, qy);
+        cm = fmaxf(cm, qx * qx + qy * qy);
+#pragma unroll
+        for (int sg = 0; sg < NS; ++sg) {
+            float wx = 1.f + qx, wy = qy;
+            if (sg) {
+                float b_x = bsx, nb_y = nbsy;
+                if (!BREG) {
+                    float b_y;
+                    lds64(Br + o2, b_x, b_y);
+                    nb_y = -b_y;
+                }
+                wx = 1.f + b_x * qx + nb_y * qy;
+                wy = b_x * qy - nb_y * qx;
+            }
+            const float nx = x[sg] * wx - y[sg] * wy;
+            y[sg] = x[sg] * wy + y[sg] * wx;
+            x[sg] = nx;
+        }
+    }
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) ex[sg] += nrm(x[sg], y[sg]);
+}
+
 template <int MPL, int NS>
 __global__ void __launch_bounds__(kClMaxThreads, 1)
     k_sample_cl(DevModel<float> md, uint64_t seed, int n_chains, int n_per_chain, int n_skip, int n_burn,
@@ -264,7 +394,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     const uint32_t rank = cluster_rank();
     const int r0 = (int)rank * TR;
     const int ntr = r0 >= nrows ? 0 : (nrows - r0 < TR ? nrows - r0 : TR);
-    const f2 one2 = f2_pack(1.f, 1.f), mone2 = f2_pack(-1.f, -1.f);
+    const f2 one2 = f2_pack(1.f, 1.f);
     const uint32_t a_s4 = (uint32_t)__cvta_generic_to_shared(s4), a_cc = (uint32_t)__cvta_generic_to_shared(cc),
                    a_bt = (uint32_t)__cvta_generic_to_shared(bt);
     uint32_t gstep = 0;   // exchanges of this cluster (parity of the exchange slots)
@@ -317,8 +447,8 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     const float c0lim = 0x1p24f / __int_as_float(s_b2);
     // e^{-4b} of the lane's units for the RBM rcur (loaded when a row of another RBM comes)
     int rcur = -1;
-    f2 bx[BREG ? NPAIR : 1], by[BREG ? NPAIR : 1];
-    float bsx = 1.f, bsy = 0.f;
+    f2 bx[BREG ? NPAIR : 1], by[BREG ? NPAIR : 1];   // e^{-4b}
+    float bsx = 1.f, nbsy = 0.f;                       // the single unit's Re e^{-4b}, -Im e^{-4b}
 #pragma unroll
     for (int i = 0; i < (BREG ? NPAIR : 1); ++i) { bx[i] = one2; by[i] = 0; }
 
@@ -506,111 +636,24 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                             rcur = r;
 #pragma unroll
                             for (int i = 0; i < NPAIR; ++i) lds128(Br + 128 * i, bx[i], by[i]);
-                            if (SGL) lds64(Br + o2, bsx, bsy);
+                            if (SGL) {
+                                float b_y;
+                                lds64(Br + o2, bsx, b_y);
+                                nbsy = -b_y;
+                            }
                         }
                         const bool big = bigf[rl] != 0;
                         float cm = 0.f;   // max_m |c_m U_m|^2
-                        f2 Rx[NS], Ry[NS];
-                        int elo[NS], ehi[NS];
-#pragma unroll
-                        for (int sg = 0; sg < NS; ++sg) { elo[sg] = 0; ehi[sg] = 0; }
-#pragma unroll
-                        for (int i = 0; i < NPAIR; ++i) {
-                            f2 ux, uy, dx, dy;
-                            lds128(Su + 128 * i, ux, uy);
-                            lds128(Sd + 128 * i, dx, dy);
-                            const f2 Ux = sub2(mul2(ux, dx), mul2(uy, dy)), Uy = fma2(ux, dy, mul2(uy, dx));
-                            f2 cx0, cy0;
-                            lds128(cr + 128 * i, cx0, cy0);
-                            if (undo) {
-                                f2 ax, ay, vx, vy;
-                                lds128(Vu + 128 * i, ax, ay);
-                                lds128(Vd + 128 * i, vx, vy);
-                                const f2 Vx = sub2(mul2(ax, vx), mul2(ay, vy)), Vy = fma2(ax, vy, mul2(ay, vx));
-                                const f2 nx = sub2(mul2(cx0, Vx), mul2(cy0, Vy));
-                                cy0 = fma2(cx0, Vy, mul2(cy0, Vx));
-                                cx0 = nx;
-                            }
-                            // c U: the cache after an acceptance, and the factor 1 + c U of sign +1
-                            const f2 qx = sub2(mul2(cx0, Ux), mul2(cy0, Uy)), qy = fma2(cx0, Uy, mul2(cy0, Ux));
-                            if (active) sts128(cr + 128 * i, qx, qy);
-                            {
-                                const f2 cq = fma2(qx, qx, mul2(qy, qy));
-                                cm = fmaxf(cm, fmaxf(f2_lo(cq), f2_hi(cq)));
-                            }
-#pragma unroll
-                            for (int sg = 0; sg < NS; ++sg) {
-                                f2 wx, wy;
-                                if (sg) {   // sign -1: 1 + c e^{-4b} U
-                                    f2 b_x, b_y;
-                                    if (BREG) { b_x = bx[i]; b_y = by[i]; }
-                                    else lds128(Br + 128 * i, b_x, b_y);
-                                    wx = fma2(b_y, mul2(qy, mone2), fma2(b_x, qx, one2));
-                                    wy = fma2(b_x, qy, mul2(b_y, qx));
-                                } else {
-                                    wx = add2(qx, one2);
-                                    wy = qy;
-                                }
-                                if (i == 0) {
-                                    Rx[sg] = wx; Ry[sg] = wy;
-                                } else {
-                                    const f2 nx = sub2(mul2(Rx[sg], wx), mul2(Ry[sg], wy));
-                                    Ry[sg] = fma2(Rx[sg], wy, mul2(Ry[sg], wx));
-                                    Rx[sg] = nx;
-                                }
-                                if (big) {   // renormalise the even and the odd units' products
-                                    float xl = f2_lo(Rx[sg]), yl = f2_lo(Ry[sg]), xh = f2_hi(Rx[sg]), yh = f2_hi(Ry[sg]);
-                                    elo[sg] += nrm(xl, yl);
-                                    ehi[sg] += nrm(xh, yh);
-                                    Rx[sg] = f2_pack(xl, xh);
-                                    Ry[sg] = f2_pack(yl, yh);
-                                }
-                            }
+                        // the row's product: uniform branches to the variant without the
+                        // undo and the per-pair renormalisation where none is needed
+                        const bool anybig = __any_sync(0xffffffffu, big);
+                        if (undo) {
+                            if (anybig) cl_row<MPL, NS, BREG, true, true>(Su, Sd, Vu, Vd, Br, cr, o2, active, bx, by, bsx, nbsy, x, y, ex, cm);
+                            else cl_row<MPL, NS, BREG, true, false>(Su, Sd, Vu, Vd, Br, cr, o2, active, bx, by, bsx, nbsy, x, y, ex, cm);
+                        } else {
+                            if (anybig) cl_row<MPL, NS, BREG, false, true>(Su, Sd, Vu, Vd, Br, cr, o2, active, bx, by, bsx, nbsy, x, y, ex, cm);
+                            else cl_row<MPL, NS, BREG, false, false>(Su, Sd, Vu, Vd, Br, cr, o2, active, bx, by, bsx, nbsy, x, y, ex, cm);
                         }
-#pragma unroll
-                        for (int sg = 0; sg < NS; ++sg) {
-                            float xl = f2_lo(Rx[sg]), yl = f2_lo(Ry[sg]), xh = f2_hi(Rx[sg]), yh = f2_hi(Ry[sg]);
-                            elo[sg] += nrm(xl, yl);
-                            ehi[sg] += nrm(xh, yh);
-                            x[sg] = xl * xh - yl * yh;
-                            y[sg] = xl * yh + yl * xh;
-                            ex[sg] = elo[sg] + ehi[sg];
-                        }
-                        if (SGL) {
-                            float ux, uy, dx, dy;
-                            lds64(Su + o2, ux, uy);
-                            lds64(Sd + o2, dx, dy);
-                            const float Ux = ux * dx - uy * dy, Uy = ux * dy + uy * dx;
-                            float c0x, c0y;
-                            lds64(cr + o2, c0x, c0y);
-                            if (undo) {
-                                float ax, ay, vx, vy;
-                                lds64(Vu + o2, ax, ay);
-                                lds64(Vd + o2, vx, vy);
-                                const float Vx = ax * vx - ay * vy, Vy = ax * vy + ay * vx;
-                                const float nx = c0x * Vx - c0y * Vy;
-                                c0y = c0x * Vy + c0y * Vx;
-                                c0x = nx;
-                            }
-                            const float qx = c0x * Ux - c0y * Uy, qy = c0x * Uy + c0y * Ux;
-                            if (active) sts64(cr + o2, qx, qy);
-                            cm = fmaxf(cm, qx * qx + qy * qy);
-#pragma unroll
-                            for (int sg = 0; sg < NS; ++sg) {
-                                float wx = 1.f + qx, wy = qy;
-                                if (sg) {
-                                    float b_x = bsx, b_y = bsy;
-                                    if (!BREG) lds64(Br + o2, b_x, b_y);
-                                    wx = 1.f + b_x * qx - b_y * qy;
-                                    wy = b_x * qy + b_y * qx;
-                                }
-                                const float nx = x[sg] * wx - y[sg] * wy;
-                                y[sg] = x[sg] * wy + y[sg] * wx;
-                                x[sg] = nx;
-                            }
-                        }
-#pragma unroll
-                        for (int sg = 0; sg < NS; ++sg) ex[sg] += nrm(x[sg], y[sg]);
                         const unsigned bal = __ballot_sync(0xffffffffu, !(cm <= c0lim));
                         if (gl == 0 && active && ((bal >> gbase) & 0xffu)) bigf[rl] = 1;
                     }
