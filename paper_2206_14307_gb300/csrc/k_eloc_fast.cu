@@ -527,12 +527,14 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
     float4 *tps = reinterpret_cast<float4 *>(smem);                                        // [K][2] x BS
     float4 *wsv = tps + (size_t)K * 2 * BS;                                                // [K][N][M] W (if staged)
     sc<float> *eps = reinterpret_cast<sc<float> *>(wsv + (ea.w_smem ? ((size_t)K * N * M + 1) / 2 : 0));   // [K][2][NB]
-    uint16_t *gbp = reinterpret_cast<uint16_t *>(eps + (size_t)K * 2 * NB);              // [nrs][NB]
+    cx<float> *csum = reinterpret_cast<cx<float> *>(eps + (size_t)K * 2 * NB);          // [K][M] sum_k W_mk
+    uint16_t *gbp = reinterpret_cast<uint16_t *>(csum + (size_t)K * M);                  // [nrs][NB]
     uint8_t *gperm = reinterpret_cast<uint8_t *>(gbp + (size_t)nrs * NB);                 // [nrs][N]
     __shared__ float s_sm[kMaxN];
     __shared__ int8_t s8[kMaxN];
     __shared__ uint16_t aa[4 * kMaxN];
-    __shared__ int n_aa;
+    __shared__ uint8_t ups[kMaxN];   // the up sites of the sample
+    __shared__ int n_aa, n_up;
     __shared__ float diag_sh;
     __shared__ sc<double> gsum[2][2 * 4 * (kEfMaxThreads / 32)];   // per (row slot, sign)
 
@@ -543,7 +545,6 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
     uint8_t *pgs = gperm + (size_t)rslot * N;
     uint16_t *bps = gbp + (size_t)rslot * NB;
     const cx<float> *Wsrc = ea.w_smem ? reinterpret_cast<const cx<float> *>(wsv) : md.Wt;
-    const f2 zero2 = 0, mone2 = f2_pack(-1.f, -1.f);
     const float sign = sg ? -1.f : 1.f;
 
     {
@@ -554,6 +555,16 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
         if (ea.w_smem) {
             cx<float> *wd = reinterpret_cast<cx<float> *>(wsv);
             for (int q = threadIdx.x; q < K * N * M; q += blockDim.x) wd[q] = md.Wt[q];
+        }
+        for (int q = threadIdx.x; q < K * M; q += blockDim.x) {
+            const int rr = q / M, m = q - rr * M;
+            cx<float> a{0.f, 0.f};
+            for (int k = 0; k < N; ++k) {
+                const cx<float> w = md.Wt[((size_t)rr * N + k) * M + m];
+                a.x += w.x;
+                a.y += w.y;
+            }
+            csum[q] = a;
         }
     }
 
@@ -585,9 +596,19 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
             }
             for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
             if (lane == 0) { n_aa = base; diag_sh = d; }
+        } else if (warp == 1) {
+            int base = 0;
+            for (int i0 = 0; i0 < N; i0 += 32) {
+                const int i = i0 + lane;
+                const bool up = i < N && s8[i] > 0;
+                const unsigned bm = __ballot_sync(0xffffffffu, up);
+                if (up) ups[base + __popc(bm & ((1u << lane) - 1u))] = (uint8_t)i;
+                base += __popc(bm);
+            }
+            if (lane == 0) n_up = base;
         }
         __syncthreads();
-        const int naa = n_aa;
+        const int naa = n_aa, nup = n_up;
 
         // waves of nrs rows; a last wave of at most nrs / 2 (nrs / 4) rows
         // gives each row 2 (4) slots, each with its share of the entries
@@ -605,25 +626,37 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
             for (int i = l8; i < N; i += 8) pgs[i] = md.perm[(size_t)g * N + i];
             for (int b = l8; b < NB; b += 8) bps[b] = md.bperm[(size_t)g * NB + b];
             __syncwarp();
-            // ---- theta': this lane's parity of unit pairs, then the partner's ----
+            // ---- theta': this lane's parity of unit pairs, then the partner's;
+            //      with s_i = +-1, theta'_m = 2 sum_{s_i = +1} W_m,g(i) - sum_k W_mk ----
             float ox[2 * NH], oy[2 * NH];
 #pragma unroll
             for (int u = 0; u < 2 * NH; ++u) { ox[u] = 0.f; oy[u] = 0.f; }
             const cx<float> *Wr = Wsrc + (size_t)r * N * M;
-            for (int i = 0; i < N; ++i) {
-                const cx<float> *wk = Wr + (size_t)pgs[i] * M;
-                const float si = s_sm[i];
+            for (int t = 0; t < nup; ++t) {
+                const cx<float> *wk = Wr + (size_t)pgs[ups[t]] * M;
 #pragma unroll
                 for (int h = 0; h < NH; ++h) {
                     const int jj = 2 * h + sg;
                     const int m = 2 * (gl + kEpGL * jj);
                     if ((M & 1) == 0 && m + 1 < M) {
                         const float4 a = *reinterpret_cast<const float4 *>(wk + m);
-                        ox[2 * h] = fmaf(si, a.x, ox[2 * h]); oy[2 * h] = fmaf(si, a.y, oy[2 * h]);
-                        ox[2 * h + 1] = fmaf(si, a.z, ox[2 * h + 1]); oy[2 * h + 1] = fmaf(si, a.w, oy[2 * h + 1]);
+                        ox[2 * h] += a.x; oy[2 * h] += a.y;
+                        ox[2 * h + 1] += a.z; oy[2 * h + 1] += a.w;
                     } else {
-                        if (m < M) { const cx<float> a = wk[m]; ox[2 * h] = fmaf(si, a.x, ox[2 * h]); oy[2 * h] = fmaf(si, a.y, oy[2 * h]); }
-                        if (m + 1 < M) { const cx<float> a = wk[m + 1]; ox[2 * h + 1] = fmaf(si, a.x, ox[2 * h + 1]); oy[2 * h + 1] = fmaf(si, a.y, oy[2 * h + 1]); }
+                        if (m < M) { const cx<float> a = wk[m]; ox[2 * h] += a.x; oy[2 * h] += a.y; }
+                        if (m + 1 < M) { const cx<float> a = wk[m + 1]; ox[2 * h + 1] += a.x; oy[2 * h + 1] += a.y; }
+                    }
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+                const int m = 2 * (gl + kEpGL * (2 * h + sg));
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (m + u < M) {
+                        const cx<float> c = csum[(size_t)r * M + m + u];
+                        ox[2 * h + u] = fmaf(2.f, ox[2 * h + u], -c.x);
+                        oy[2 * h + u] = fmaf(2.f, oy[2 * h + u], -c.y);
                     }
                 }
             }
@@ -650,91 +683,114 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
                     at.y += __shfl_xor_sync(0xffffffffu, at.y, o);
                 }
             }
-            // ---- this group's sign: p, q = 1/p - 1, the p product and the row term ----
-            f2 ca[NP], cb[NP], cc[NP];
-            sc<float> prod{1.f, 0.f, 0};
-            f2 Px = 0, Py = 0;
-            bool small = ea.plain != 0;
+            // ---- this group's sign.  With q_m = e^{-2 theta_m} = (1 - p_m)/p_m the
+            //      unit factor is p_m (q_m + U_m), and 2 cosh(theta_m) p_m = e^{theta_m}:
+            //      the row's term times prod_m p_m is lead e^{sum_m theta_m}, and its
+            //      term is that times prod_m (1 + q_m) ----
+            f2 ca[NP], cb[NP];
+            float stx = 0.f, sty = 0.f;   // sum of theta over the lane's units
+            f2 Qx = f2_pack(1.f, 1.f), Qy = 0;
+            int qlo = 0, qhi = 0;         // exponents of the even and odd units' products of 1 + q
+            bool small = ea.plain != 0;   // some |p| < 2^-12 (|1 + q| > 2^12): the plain factors
             const cx<float> *br = md.bvec + (size_t)r * M;
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                float pxv[2], pyv[2];
+                float qxv[2], qyv[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int m = 2 * (gl + kEpGL * j) + h;
-                    pxv[h] = 1.f; pyv[h] = 0.f;   // units past M: p = 1, q = 0 (their U is 1)
+                    qxv[h] = 0.f; qyv[h] = 0.f;   // units past M: q = 0 (their U is 1)
                     if (m < M) {
                         cx<float> th{sign * tx[2 * j + h], sign * ty[2 * j + h]};
                         if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
-                        cx<float> mant, pv;
-                        int k;
-                        cosh2(th, mant, k, pv);
-                        pxv[h] = pv.x; pyv[h] = pv.y;
-                        const cx<float> q = cmul(mk(prod.x, prod.y), mant);
-                        prod = sc<float>{q.x, q.y, prod.e + k};
-                        small = small || !(pv.x * pv.x + pv.y * pv.y >= 0x1p-24f);
+                        stx += th.x;
+                        sty += th.y;
+                        const float e = exp2f(-2.8853900817779268f * th.x);   // e^{-2 Re theta}
+                        float sn, cs;
+                        sincosf(2.f * th.y, &sn, &cs);
+                        qxv[h] = e * cs;
+                        qyv[h] = -e * sn;
+                        const float ax = 1.f + qxv[h];
+                        small = small || !(ax * ax + qyv[h] * qyv[h] <= 0x1p24f);
                     }
                 }
-                const f2 px = f2_pack(pxv[0], pxv[1]), py = f2_pack(pyv[0], pyv[1]);
-                const f2 pden = fma2(px, px, mul2(py, py));
-                const f2 inv = f2_pack(__frcp_rn(f2_lo(pden)), __frcp_rn(f2_hi(pden)));
-                ca[j] = fma2(px, inv, mone2);              // q = 1/p - 1
-                cb[j] = mul2(sub2(zero2, py), inv);
-                cc[j] = px;   // (p kept for the plain form)
-                if (j == 0) {
-                    Px = px; Py = py;
-                } else {
-                    const f2 nx = sub2(mul2(Px, px), mul2(Py, py));
-                    Py = fma2(Px, py, mul2(Py, px));
-                    Px = nx;
+                ca[j] = f2_pack(qxv[0], qxv[1]);
+                cb[j] = f2_pack(qyv[0], qyv[1]);
+                const f2 fx = add2(ca[j], f2_pack(1.f, 1.f));
+                const f2 nx = sub2(mul2(Qx, fx), mul2(Qy, cb[j]));
+                Qy = fma2(Qx, cb[j], mul2(Qy, fx));
+                Qx = nx;
+                if ((j % 3) == 2 || j == NP - 1) {
+                    float xl = f2_lo(Qx), yl = f2_lo(Qy), xh = f2_hi(Qx), yh = f2_hi(Qy);
+                    qlo += nrm(xl, yl);
+                    qhi += nrm(xh, yh);
+                    Qx = f2_pack(xl, xh);
+                    Qy = f2_pack(yl, yh);
                 }
-                (void)py;
             }
-            prod = group_prod<kEpGL>(prod);
             const cx<float> lc = md.logc[r];
-            sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
             float chg = md.chi[g];
             if (sg && md.chiP < 0) chg = -chg;
-            lead.x *= chg; lead.y *= chg;
-            const sc<float> wt = sc_mul(prod, sc_norm(lead));
-            if (gl == 0 && active && part == 0)
-                gsum[1][gslot] = sc_add(gsum[1][gslot], sc<double>{(double)wt.x, (double)wt.y, wt.e});
 
             float accx = 0.f, accy = 0.f;
             double Ox = 0.0, Oy = 0.0;
             sc<float> mult;
             if (!__any_sync(0xffffffffu, small)) {
-                const float u = f2_lo(Px) * f2_hi(Px) - f2_lo(Py) * f2_hi(Py);
-                const float v = f2_lo(Px) * f2_hi(Py) + f2_lo(Py) * f2_hi(Px);
-                const sc<float> Pp = group_prod<kEpGL>(sc<float>{u, v, 0});
-                ep_entries<NP, true>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, BS, ca, cb, cc, Pp.e, gl, gbase, accx,
-                                     accy, Ox, Oy);
-                mult = sc_mul(wt, sc<float>{Pp.x, Pp.y, 0});
+                // sum of theta and prod (1 + q) over the group's 4 lanes
+#pragma unroll
+                for (int o = 1; o < kEpGL; o <<= 1) {
+                    stx += __shfl_xor_sync(0xffffffffu, stx, o);
+                    sty += __shfl_xor_sync(0xffffffffu, sty, o);
+                }
+                float u = f2_lo(Qx) * f2_hi(Qx) - f2_lo(Qy) * f2_hi(Qy);
+                float v = f2_lo(Qx) * f2_hi(Qy) + f2_lo(Qy) * f2_hi(Qx);
+                const int qe = qlo + qhi + nrm(u, v);
+                const sc<float> Q = group_prod<kEpGL>(sc<float>{u, v, qe});
+                // lead e^{sum theta} = term x prod p, kept as mantissa x 2^(e + Q.e) and
+                // the entries scaled by 2^-Q.e (near 2^0, as prod (q + U) ~ prod (1 + q))
+                sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x + stx, lc.y + sign * at.y + sty});
+                lead.x *= chg; lead.y *= chg;
+                lead = sc_norm(lead);
+                const sc<float> wt = sc_mul(lead, Q);   // the row term
+                if (gl == 0 && active && part == 0)
+                    gsum[1][gslot] = sc_add(gsum[1][gslot], sc<double>{(double)wt.x, (double)wt.y, wt.e});
+                ep_entries<NP, true>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, BS, ca, cb, cb, -Q.e, gl,
+                                     gbase, accx, accy, Ox, Oy);
+                mult = sc<float>{lead.x, lead.y, lead.e + Q.e};
             } else {
-                // the plain factors 1 + p (U - 1): p from q (p = 1 / (1 + q)) would lose the
-                // small p, so take it from the kept copy and the product's imaginary parts
+                // the plain factors 1 + p (U - 1) with p and prod 2 cosh(theta) from cosh2
+                f2 cc[NP];
+                sc<float> prod{1.f, 0.f, 0};
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    float pyv[2];
+                    float pxv[2], pyv[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int m = 2 * (gl + kEpGL * j) + h;
-                        pyv[h] = 0.f;
+                        pxv[h] = 1.f; pyv[h] = 0.f;   // units past M: p = 1 (their U is 1)
                         if (m < M) {
                             cx<float> th{sign * tx[2 * j + h], sign * ty[2 * j + h]};
                             if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
                             cx<float> mant, pv;
                             int k;
                             cosh2(th, mant, k, pv);
-                            pyv[h] = pv.y;
+                            pxv[h] = pv.x; pyv[h] = pv.y;
+                            const cx<float> z = cmul(mk(prod.x, prod.y), mant);
+                            prod = sc_norm(sc<float>{z.x, z.y, prod.e + k});
                         }
                     }
-                    ca[j] = cc[j];
+                    ca[j] = f2_pack(pxv[0], pxv[1]);
                     cb[j] = f2_pack(pyv[0], pyv[1]);
                     cc[j] = f2_pack(-pyv[0], -pyv[1]);
                 }
-                ep_entries<NP, false>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, BS, ca, cb, cc, 0, gl, gbase, accx,
-                                      accy, Ox, Oy);
+                prod = group_prod<kEpGL>(prod);
+                sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
+                lead.x *= chg; lead.y *= chg;
+                const sc<float> wt = sc_mul(prod, sc_norm(lead));
+                if (gl == 0 && active && part == 0)
+                    gsum[1][gslot] = sc_add(gsum[1][gslot], sc<double>{(double)wt.x, (double)wt.y, wt.e});
+                ep_entries<NP, false>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, BS, ca, cb, cc, 0, gl,
+                                      gbase, accx, accy, Ox, Oy);
                 mult = wt;
             }
             double ax = (double)accx + Ox, ay = (double)accy + Oy;
@@ -833,7 +889,8 @@ static size_t ef_smem(const DevModel<float> &md, const EfLayout &L, int warps)
 {
     const size_t tab = (size_t)md.K * 2 * L.BS * sizeof(float4);
     const size_t wst = L.w_smem ? ((size_t)md.K * md.N * md.M + 1) / 2 * sizeof(float4) : 0;
-    return tab + wst + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) +
+    const size_t cs = L.pair ? (size_t)md.K * md.M * sizeof(cx<float>) : 0;   // column sums of W
+    return tab + wst + (size_t)md.K * 2 * md.nbonds * sizeof(sc<float>) + cs +
            (size_t)warps * 4 * (md.nbonds * sizeof(uint16_t) + md.N);
 }
 
