@@ -108,8 +108,9 @@ FP64_PEAK_TFLOPS = float(ALU_PEAKS["fp64_fma_tflops"])
 FLOPS_PER_ELEMENT = 16
 # DRAM bytes (read + write) of one full launch of the kernel a roofline names,
 # from ncu captures of the current kernel (None: not captured since it last
-# changed).
-K_RATIO_TRAFFIC = None
+# changed).  k_eloc_pair: 680.96 KB read, 0 written in a timed-step launch of
+# the 6x6 bench (16,384 samples; profiles/vmc_step_6x6.md).
+K_RATIO_TRAFFIC = 680960
 K_LANCZOS_TRAFFIC = None
 # Shared-memory bandwidth of the SMs, 128 B per clock per SM at the maximum SM
 # clock (derived, not measured): the roof of the sampler's cache stream.
@@ -728,9 +729,9 @@ def main():
                               "cluster of CTAs for larger models; one CTA here)",
                     "bound": "latency",
                     "bound_note": "each Metropolis step of a chain is serial: the ratio pass over the chain's "
-                                  "cache, the CTA's sum, the decision and the next proposal (ncu: wait, "
-                                  "short_scoreboard and barrier stalls); DRAM carries only the tables and the "
-                                  "kept samples",
+                                  "cache, the CTA's sum, the decision and the next proposal (ncu: not_selected, "
+                                  "barrier, wait and math-pipe-throttle stalls); DRAM carries only the tables and "
+                                  "the kept samples",
                     "achieved": samp_bytes / samp_s / 1e9, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
                     "frac": samp_bytes / samp_s / 1e9 / SMEM_PEAK_GBS,
                     "frac_kind": "algorithmic cache stream (8 K|G|M (1 + acceptance) B per proposal) read from "
