@@ -1,10 +1,12 @@
-"""The FP32 sampler with each chain's cache in the shared memory of a
-thread-block cluster (one CTA per SM, the chain's (row, sign) pairs split over
-the cluster's CTAs, the ratio's partial sums exchanged through distributed
-shared memory).  Proposals are Philox-exact and accept decisions equal the FP64
+"""The FP32 sampler with each chain's cache in shared memory: one CTA per SM,
+the chain's rows (r, g) split over the CTAs of a thread-block cluster when
+they do not fit one CTA, the partial sums exchanged through distributed shared
+memory.  Proposals are Philox-exact and accept decisions equal the FP64
 oracle's except at near-ties, for the cluster sizes the models select (1 at
-4x4, 2 at the 6x6 workload, 4 at 8x8 M = 128) and for forced sizes (test hook
-NNQS_TEST_SAMPLER_CLUSTER), including CTAs that own no pair."""
+4x4 and at the 6x6 workload, 8 at 8x8 M = 128) and for forced sizes (test hook
+NNQS_TEST_SAMPLER_CLUSTER), including CTAs that own no row, and with
+parameters large enough that some cache entries exceed 2^12 in modulus (the
+rows' products are then renormalised after every unit pair)."""
 import os
 
 import numpy as np
@@ -53,11 +55,12 @@ def replay(om, gm, N, seed, nc, T):
 
 
 @pytest.mark.parametrize("L,M,proj,inv,std,force,nc,T", [
-    (6, 72, True, 1, 0.05, "", 3, 80),      # the 6x6 workload shape: cluster of 2
-    (8, 128, True, 0, 0.05, "", 1, 30),     # 8x8, M = 128: cluster of 4
-    (4, 8, False, 0, 0.3, "4", 3, 150),     # one pair over a cluster of 4: three CTAs own none
-    (4, 6, True, 1, 0.3, "8", 3, 150),      # 256 pairs over a cluster of 8
+    (6, 72, True, 1, 0.05, "", 3, 80),      # the 6x6 workload shape: one CTA
+    (8, 128, True, 0, 0.05, "", 1, 30),     # 8x8, M = 128: cluster of 8
+    (4, 8, False, 0, 0.3, "4", 3, 150),     # one row over a cluster of 4: three CTAs own none
+    (4, 6, True, 1, 0.3, "8", 3, 150),      # 128 rows over a cluster of 8
     (6, 12, True, -1, 0.3, "2", 3, 150),
+    (4, 8, True, 1, 1.0, "", 3, 120),       # |c| beyond 2^12: rows renormalised after every unit pair
 ])
 def test_cluster_sampler_replays_oracle(cluster_env, L, M, proj, inv, std, force, nc, T):
     cluster_env(force)
