@@ -482,8 +482,8 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
         }
         __syncthreads();
 
-        // ---- fresh cache of this CTA's rows: c = 1/p(theta') - 1 per unit of
-        //      sign +1, tc per pair, and the chain's sum of terms ----
+        // ---- fresh cache of this CTA's rows: c = e^{-2 theta'} = 1/p(theta') - 1
+        //      per unit of sign +1, tc per pair, and the chain's sum of terms ----
         sc<float> so{0.f, 0.f, 0};
         for (int tb = 0; tb < ntr; tb += nslots) {
             const int rl0 = tb + slot;
@@ -519,7 +519,11 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
 #pragma unroll
             for (int sg = 0; sg < NS; ++sg) {
                 const float sign = sg ? -1.f : 1.f;
-                sc<float> prod{1.f, 0.f, 0}, pp{1.f, 0.f, 0};
+                // c = e^{-2 theta'} directly (no cancellation where p(theta') is near 1);
+                // 2 cosh(theta') p(theta') = e^{theta'}, so tc = lead e^{sum theta'} and
+                // the term is tc prod_m (1 + c_m)
+                float stx = 0.f, sty = 0.f;
+                sc<float> qp{1.f, 0.f, 0};
 #pragma unroll
                 for (int j = 0; j < MPL; ++j) {
                     const int m = gl + kCGL * j;
@@ -528,19 +532,18 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                         // theta' = -(x + b) for sigma = +1, -x + b for sigma = -1
                         cx<float> th{-xs[j].x, -xs[j].y};
                         if (md.use_bias) { const cx<float> b = br[m]; th.x -= sign * b.x; th.y -= sign * b.y; }
-                        cx<float> mant, pv;
-                        int k;
-                        cosh2(th, mant, k, pv);
-                        const cx<float> z = cmul(mk(prod.x, prod.y), mant);
-                        prod = sc_norm(sc<float>{z.x, z.y, prod.e + k});
-                        pp = sc_mul(pp, sc<float>{pv.x, pv.y, 0});
-                        const float d = pv.x * pv.x + pv.y * pv.y;
-                        if (d > 0.f) {
-                            const float id = 1.f / d;
-                            c = cx<float>{pv.x * id - 1.f, -pv.y * id};
-                        } else {
-                            c = cx<float>{0x1p60f, 0.f};   // p(theta') = 0 (the unit's factor does not use c)
+                        stx += th.x;
+                        sty += th.y;
+                        float a2 = -2.8853900817779268f * th.x;   // log2 |c|
+                        if (!(a2 <= 100.f)) {   // |c| beyond 2^100: outside the cache's FP32 range
+                            flag_range(md.status);
+                            a2 = 100.f;
                         }
+                        const float e = exp2f(a2);
+                        float sn, cs;
+                        sincosf(-2.f * th.y, &sn, &cs);
+                        c = cx<float>{e * cs, e * sn};
+                        qp = sc_mul(qp, sc<float>{1.f + c.x, c.y, 0});
                         big = big || !(c.x * c.x + c.y * c.y <= 0x1p24f);
                     }
                     if (sg == 0) {   // the row keeps c of sign +1 only: c(-1) = c(+1) e^{-4b}
@@ -549,17 +552,21 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                         if (active) { cf[ore] = c.x; cf[oim] = c.y; }
                     }
                 }
-                prod = group_prod<kCGL>(prod);
-                pp = group_prod<kCGL>(pp);
+#pragma unroll
+                for (int o = kCGL / 2; o > 0; o >>= 1) {
+                    stx += shfl_x(stx, o);
+                    sty += shfl_x(sty, o);
+                }
+                qp = group_prod<kCGL>(qp);
                 if (gl == 0 && active) {
                     const cx<float> lc = md.logc[r];
-                    sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
+                    sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x + stx, lc.y + sign * at.y + sty});
                     float ch = md.chi[g];
                     if (sg && md.chiP < 0) ch = -ch;
                     lead.x *= ch; lead.y *= ch;
-                    const sc<float> tm = sc_mul(prod, sc_norm(lead));
-                    tcb[rl * NS + sg] = sc_mul(tm, pp);
-                    so = sc_add(so, tm);
+                    lead = sc_norm(lead);
+                    tcb[rl * NS + sg] = lead;
+                    so = sc_add(so, sc_mul(lead, qp));
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, big);
