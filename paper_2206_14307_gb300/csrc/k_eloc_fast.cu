@@ -11,8 +11,12 @@
 //   E_loc = diag(s) + [sum_t w_t P_t sum_b (J_b/2) e^{C_b} prod_m (q_m + U_m)]
 //                     / [sum_t w_t],
 // w_t = c_r chi(g) chi_P e^{+-a.T_g s} prod_m 2cosh(theta_m) the row's term and
-// P_t = prod_m p_m.  A row whose group has some |p_m| < 2^-12 (q above 2^12)
-// takes the plain factors 1 + p_m (U_m - 1) instead.
+// P_t = prod_m p_m.  q = e^{-2 theta} is formed directly (1/p - 1 would lose
+// its relative precision where p is near 1), and as 2cosh(theta) p = e^theta,
+// w_t P_t = c_r chi(g) chi_P e^{+-a.T_g s + sum_m theta_m} and w_t is that
+// times prod_m (1 + q_m): no cosh or division on this path.  A row whose group
+// has some |p_m| < 2^-12 (|1 + q| above 2^12) takes the plain factors
+// 1 + p_m (U_m - 1) instead, with p from cosh2.
 //
 // Layout: one CTA per SM (the tables of one model, 2 x 4N rows per RBM, are
 // copied into its shared memory once), one sample at a time.  A group of 8
@@ -176,7 +180,6 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
     const int gidx = warp * NG + grp, ngroups = nwarps * NG;
     uint8_t *pgs = gperm + (size_t)gidx * N;
     uint16_t *bps = gbp + (size_t)gidx * NB;
-    const f2 zero2 = 0, mone2 = f2_pack(-1.f, -1.f);
 
     // tables into shared memory (once per CTA)
     {
@@ -269,78 +272,89 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
             }
             for (int sg = 0; sg < md.nsign; ++sg) {
                 const float sign = sg ? -1.f : 1.f;
-                // ---- p of the lane's units, q = 1/p - 1, the p product and the row term ----
-                f2 ca[NP], cb[NP], cc[NP];
-                sc<float> prod{1.f, 0.f, 0};
-                f2 Px = 0, Py = 0;
-                bool small = ea.plain != 0;   // some |p| < 2^-12: the plain factors for this row
+                // ---- q_m = e^{-2 theta_m} = (1 - p_m)/p_m of the lane's units; the row's
+                //      term x prod_m p_m is lead e^{sum_m theta_m} (2 cosh(theta) p = e^theta)
+                //      and its term that times prod_m (1 + q_m) ----
+                f2 ca[NP], cb[NP];
+                float stx = 0.f, sty = 0.f;
+                f2 Qx = f2_pack(1.f, 1.f), Qy = 0;
+                int qlo = 0, qhi = 0;
+                bool small = ea.plain != 0;   // some |p| < 2^-12 (|1 + q| > 2^12): the plain factors
                 const cx<float> *br = md.bvec + (size_t)r * M;
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    float pxv[2], pyv[2];
+                    float qxv[2], qyv[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int m = 2 * (gl + kEfGL * j) + h;
-                        pxv[h] = 0.f; pyv[h] = 0.f;
+                        qxv[h] = 0.f; qyv[h] = 0.f;   // units past M: q = 0 (their U is 1)
                         if (m < M) {
                             cx<float> th{sign * tx[2 * j + h], sign * ty[2 * j + h]};
                             if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
-                            cx<float> mant, pv;
-                            int k;
-                            cosh2(th, mant, k, pv);
-                            pxv[h] = pv.x; pyv[h] = pv.y;
-                            const cx<float> q = cmul(mk(prod.x, prod.y), mant);
-                            prod = sc<float>{q.x, q.y, prod.e + k};
-                            small = small || !(pv.x * pv.x + pv.y * pv.y >= 0x1p-24f);
+                            stx += th.x;
+                            sty += th.y;
+                            const float e = exp2f(-2.8853900817779268f * th.x);   // e^{-2 Re theta}
+                            float sn, cs;
+                            sincosf(2.f * th.y, &sn, &cs);
+                            qxv[h] = e * cs;
+                            qyv[h] = -e * sn;
+                            const float ax = 1.f + qxv[h];
+                            small = small || !(ax * ax + qyv[h] * qyv[h] <= 0x1p24f);
                         }
                     }
-                    // units past M: p = 1, q = 0 (their U is 1)
-                    const int m0 = 2 * (gl + kEfGL * j);
-                    if (m0 >= M) { pxv[0] = 1.f; pyv[0] = 0.f; }
-                    if (m0 + 1 >= M) { pxv[1] = 1.f; pyv[1] = 0.f; }
-                    const f2 px = f2_pack(pxv[0], pxv[1]), py = f2_pack(pyv[0], pyv[1]);
-                    const f2 pden = fma2(px, px, mul2(py, py));
-                    const f2 inv = f2_pack(__frcp_rn(f2_lo(pden)), __frcp_rn(f2_hi(pden)));
-                    const f2 qx = fma2(px, inv, mone2), qy = mul2(sub2(zero2, py), inv);   // q = 1/p - 1
-                    const f2 pfx = px, pfy = py;
-                    if (j == 0) {
-                        Px = pfx; Py = pfy;
-                    } else {
-                        const f2 nx = sub2(mul2(Px, pfx), mul2(Py, pfy));
-                        Py = fma2(Px, pfy, mul2(Py, pfx));
-                        Px = nx;
+                    ca[j] = f2_pack(qxv[0], qxv[1]);
+                    cb[j] = f2_pack(qyv[0], qyv[1]);
+                    const f2 fx = add2(ca[j], f2_pack(1.f, 1.f));
+                    const f2 nx = sub2(mul2(Qx, fx), mul2(Qy, cb[j]));
+                    Qy = fma2(Qx, cb[j], mul2(Qy, fx));
+                    Qx = nx;
+                    if ((j % 3) == 2 || j == NP - 1) {
+                        float xl = f2_lo(Qx), yl = f2_lo(Qy), xh = f2_hi(Qx), yh = f2_hi(Qy);
+                        qlo += nrm(xl, yl);
+                        qhi += nrm(xh, yh);
+                        Qx = f2_pack(xl, xh);
+                        Qy = f2_pack(yl, yh);
                     }
-                    ca[j] = qx; cb[j] = qy;
                 }
-                prod = group_prod<kEfGL>(prod);
                 const cx<float> lc = md.logc[r];
-                sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
                 float chg = md.chi[g];
                 if (sg && md.chiP < 0) chg = -chg;
-                lead.x *= chg; lead.y *= chg;
-                const sc<float> wt = sc_mul(prod, sc_norm(lead));   // the row term (same in every lane)
-                if (gl == 0 && active && part == 0)
-                    gsum[1][gidx] = sc_add(gsum[1][gidx], sc<double>{(double)wt.x, (double)wt.y, wt.e});
 
                 float accx = 0.f, accy = 0.f;
                 double Ox = 0.0, Oy = 0.0;
                 sc<float> mult;
                 if (!__any_sync(0xffffffffu, small)) {
-                    const float u = f2_lo(Px) * f2_hi(Px) - f2_lo(Py) * f2_hi(Py);
-                    const float v = f2_lo(Px) * f2_hi(Py) + f2_lo(Py) * f2_hi(Px);
-                    const sc<float> Pp = group_prod<kEfGL>(sc<float>{u, v, 0});
-                    ef_entries<NP, true>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, ca, cb, cc, Pp.e, gl, gbase, accx, accy,
-                                         Ox, Oy);
-                    mult = sc_mul(wt, sc<float>{Pp.x, Pp.y, 0});
+#pragma unroll
+                    for (int o = 1; o < kEfGL; o <<= 1) {
+                        stx += __shfl_xor_sync(0xffffffffu, stx, o);
+                        sty += __shfl_xor_sync(0xffffffffu, sty, o);
+                    }
+                    float u = f2_lo(Qx) * f2_hi(Qx) - f2_lo(Qy) * f2_hi(Qy);
+                    float v = f2_lo(Qx) * f2_hi(Qy) + f2_lo(Qy) * f2_hi(Qx);
+                    const int qe = qlo + qhi + nrm(u, v);
+                    const sc<float> Q = group_prod<kEfGL>(sc<float>{u, v, qe});
+                    // lead e^{sum theta} = term x prod p, as mantissa x 2^(e + Q.e), with the
+                    // entries scaled by 2^-Q.e (near 2^0, as prod (q + U) ~ prod (1 + q))
+                    sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x + stx, lc.y + sign * at.y + sty});
+                    lead.x *= chg; lead.y *= chg;
+                    lead = sc_norm(lead);
+                    const sc<float> wt = sc_mul(lead, Q);   // the row term
+                    if (gl == 0 && active && part == 0)
+                        gsum[1][gidx] = sc_add(gsum[1][gidx], sc<double>{(double)wt.x, (double)wt.y, wt.e});
+                    ef_entries<NP, true>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, ca, cb, cb, -Q.e, gl,
+                                         gbase, accx, accy, Ox, Oy);
+                    mult = sc<float>{lead.x, lead.y, lead.e + Q.e};
                 } else {
-                    // p again, for the plain factors
+                    // the plain factors 1 + p (U - 1) with p and prod 2 cosh(theta) from cosh2
+                    f2 cc[NP];
+                    sc<float> prod{1.f, 0.f, 0};
 #pragma unroll
                     for (int j = 0; j < NP; ++j) {
                         float pxv[2], pyv[2];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int m = 2 * (gl + kEfGL * j) + h;
-                            pxv[h] = 0.f; pyv[h] = 0.f;
+                            pxv[h] = 1.f; pyv[h] = 0.f;   // units past M: p = 1 (their U is 1)
                             if (m < M) {
                                 cx<float> th{sign * tx[2 * j + h], sign * ty[2 * j + h]};
                                 if (md.use_bias) { const cx<float> b = br[m]; th.x += b.x; th.y += b.y; }
@@ -348,14 +362,22 @@ __global__ void __launch_bounds__(kEfMaxThreads, 1)
                                 int k;
                                 cosh2(th, mant, k, pv);
                                 pxv[h] = pv.x; pyv[h] = pv.y;
+                                const cx<float> z = cmul(mk(prod.x, prod.y), mant);
+                                prod = sc_norm(sc<float>{z.x, z.y, prod.e + k});
                             }
                         }
                         ca[j] = f2_pack(pxv[0], pxv[1]);
                         cb[j] = f2_pack(pyv[0], pyv[1]);
                         cc[j] = f2_pack(-pyv[0], -pyv[1]);
                     }
-                    ef_entries<NP, false>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, ca, cb, cc, 0, gl, gbase, accx, accy,
-                                          Ox, Oy);
+                    prod = group_prod<kEfGL>(prod);
+                    sc<float> lead = sc_exp(cx<float>{lc.x + sign * at.x, lc.y + sign * at.y});
+                    lead.x *= chg; lead.y *= chg;
+                    const sc<float> wt = sc_mul(prod, sc_norm(lead));
+                    if (gl == 0 && active && part == 0)
+                        gsum[1][gidx] = sc_add(gsum[1][gidx], sc<double>{(double)wt.x, (double)wt.y, wt.e});
+                    ef_entries<NP, false>(md, tps, eps, aa + e_lo, bps, e_n, e_max, r, sg, MH, ca, cb, cc, 0, gl,
+                                          gbase, accx, accy, Ox, Oy);
                     mult = wt;
                 }
                 double ax = (double)accx + Ox, ay = (double)accy + Oy;

@@ -5,7 +5,8 @@ NNQS_TEST_ELOC_ENGINE=old), on the 6x6 workload shape and on shapes with
 several RBMs, no biases, odd inversion and a B1 irrep; the plain factors
 1 + p (U - 1) (taken where some |p| < 2^-12; forced by NNQS_TEST_ELOC_PLAIN=1)
 are checked the same way; both engines are also checked against the FP64
-oracle on a few samples."""
+oracle on a few samples (at std 1.0, within 10x the general engine's own
+distance from it)."""
 import os
 
 import numpy as np
@@ -25,6 +26,8 @@ pytestmark = pytest.mark.gpu
     (4, 2, 12, -1, True, 2, 0.2, 300, "1"),
     (4, 1, 16, 0, True, 0, 0.3, 300, None),
     (6, 1, 36, 1, True, 0, 0.05, 300, None),
+    (4, 1, 16, 0, True, 0, 1.0, 100, None),     # large parameters: |q| far from 1 both ways
+    (4, 1, 16, 1, True, 0, 1.0, 100, None),
 ])
 def test_fast_eloc_matches_general_engine(L, K, M, inv, bias, irrep, std, n, plain):
     N = L * L
@@ -48,7 +51,16 @@ def test_fast_eloc_matches_general_engine(L, K, M, inv, bias, irrep, std, n, pla
         else:
             os.environ["NNQS_TEST_ELOC_ENGINE"] = old
     gm.status()
-    tol = 1e-5 if std <= 0.05 else 1e-4
-    assert np.max(np.abs(fast - gen) / (np.abs(gen) + 1)) <= tol
-    want = om.local_energy(s[:4])
-    assert np.max(np.abs(fast[:4] - want) / (np.abs(want) + 1)) <= tol
+    if std <= 0.3:
+        tol = 1e-5 if std <= 0.05 else 1e-4
+        assert np.max(np.abs(fast - gen) / (np.abs(gen) + 1)) <= tol
+        want = om.local_energy(s[:4])
+        assert np.max(np.abs(fast[:4] - want) / (np.abs(want) + 1)) <= tol
+    else:
+        # std 1.0: E_loc reaches 1e6 through cancelling ratios, beyond what FP32
+        # holds; on every sample the fast engine is held to the general FP32
+        # engine's own distance from the FP64 oracle
+        want = om.local_energy(s)
+        err = np.abs(fast - want) / (np.abs(want) + 1)
+        err_gen = np.abs(gen - want) / (np.abs(want) + 1)
+        assert np.all(err <= 10 * err_gen + 1e-5), (np.max(err), np.max(err_gen))
