@@ -69,8 +69,8 @@ WORKLOAD = "6x6 J1-J2 (J2/J1=0.5), complex RBM alpha=2 (M=72), 288 ops + spin in
 
 
 def _measured_peaks():
-    """HBM GB/s and dense bf16 TFLOP/s (burst) measured on the GB300s,
-    from MEASURED_PEAKS.json beside this file; else the fallback figures."""
+    """HBM GB/s and dense bf16 TFLOP/s (burst) measured on GB300s, from
+    MEASURED_PEAKS.json beside this file; else the fallback figures."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
@@ -83,8 +83,8 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 
 
 def _alu_peaks():
-    """FP32 FMA / MUFU / FP64 peaks measured on this machine's GB300 by the
-    microbenchmark summarised in profiles/alu_peaks_gb300.md (its JSON line);
+    """FP32 FMA / MUFU / FP64 peaks measured on a GB300 by the microbenchmark
+    summarised in profiles/alu_peaks_gb300.md (its JSON line);
     else the peak derived from the unit counts and the maximum SM clock."""
     try:
         with open(os.path.join(ROOT, "profiles", "alu_peaks_gb300.md")) as f:
