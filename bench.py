@@ -112,9 +112,12 @@ FLOPS_PER_ELEMENT = 16
 # the 6x6 bench (16,384 samples; profiles/vmc_step_6x6.md).
 K_RATIO_TRAFFIC = 680960
 K_LANCZOS_TRAFFIC = None
-# Shared-memory bandwidth of the SMs, 128 B per clock per SM at the maximum SM
-# clock (derived, not measured): the roof of the sampler's cache stream.
-SMEM_PEAK_GBS = 128 * 152 * 2.07
+# Shared-memory bandwidth of the SMs (conflict-free 128-bit loads, measured by
+# bench_peaks.cu; else 128 B per clock per SM at the maximum SM clock): the
+# roof of the sampler's cache stream.
+SMEM_PEAK_GBS = float(ALU_PEAKS.get("smem_lds128_gbs", 128 * 152 * 2.07))
+SMEM_SOURCE = "measured (profiles/alu_peaks_gb300.md)" if "smem_lds128_gbs" in ALU_PEAKS else \
+    "derived: 128 B/clock/SM at 2.07 GHz"
 
 
 LZ_L, LZ_M, LZ_SAMPLES, LZ_SUBSET = 8, 128, 4096, 912   # subset: 6 x 152 SMs
@@ -735,7 +738,8 @@ def main():
                     "achieved": samp_bytes / samp_s / 1e9, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
                     "frac": samp_bytes / samp_s / 1e9 / SMEM_PEAK_GBS,
                     "frac_kind": "algorithmic cache stream (8 K|G|M (1 + acceptance) B per proposal) read from "
-                                 "shared memory, against 128 B/clock/SM at 2.07 GHz (derived)",
+                                 "shared memory, against the shared-memory bandwidth of 128-bit loads",
+                    "peak_source": SMEM_SOURCE,
                     "traffic": None,
                     "work": f"{proposals} proposals x {samp_per:.0f} B", "ms": res["ms_sample"]},
         "e2e": {"value": world * res["evals"] / (e2e_ms / 1e3), "unit": "amplitude evals/s",
