@@ -141,8 +141,9 @@ int nnqs_set_params_device(nnqs_model *model, const double *params, int64_t P, v
  *          (may be NULL).
  * The FP32 form keeps each chain's cache in the shared memory of one CTA (or
  * of a thread-block cluster, for caches larger than one CTA holds); a cache
- * entry outside its FP32 range (a hidden bias with |Re b| > 20, or an entry
- * e^{-2 theta} beyond 2^100) sets NNQS_ERANGE in the status word.
+ * entry outside its FP32 range (an entry e^{-2 theta} beyond 2^100 or, with
+ * spin inversion, a hidden bias with |Re b| > 20) sets NNQS_ERANGE in the
+ * status word.
  * Errors: NNQS_EINVAL (non-positive counts), NNQS_ENOMEM (chain caches). */
 int nnqs_sample(nnqs_model *model, uint64_t seed, int32_t n_chains, int32_t n_per_chain,
                 int32_t n_skip, int32_t n_burn, uint64_t *cfg_out, float *acc_out, void *stream);
